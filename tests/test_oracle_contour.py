@@ -1,0 +1,63 @@
+"""Pins for the quadrature nodes, weights and rational function of Eq. 7 (CPU only)."""
+import numpy as np
+import pytest
+
+from oracle import contour
+
+
+@pytest.mark.parametrize("n", [4, 7, 32])
+def test_circle_closed_form(n):
+    """alpha = 1 (a circle): the N-point rule with the half-step offset of Eq. 7 sums
+    the geometric series exactly, P_N(lambda) = 1 / (1 + ((lambda - gamma)/rho)^N)."""
+    gam, rho = 0.7, 1.3
+    z, p = contour.projector_coefficients(n, gam, rho, 1.0)
+    lam = np.array([-2.0, -0.3, 0.1, 0.69, 1.5, 1.99, 2.5, 4.0])
+    got = contour.rational(lam, z, p, 0.0)
+    want = 1.0 / (1.0 + ((lam - gam) / rho) ** n)
+    assert np.abs(got - want).max() < 1e-14
+
+
+def test_nodes_match_eq7_parametrisation():
+    z, w = contour.ellipse_nodes(8, 1.2, 1.1999, 0.1)
+    th = 2 * np.pi * (np.arange(1, 9) - 0.5) / 8
+    assert np.allclose(z.real, 1.2 + 1.1999 * np.cos(th))
+    assert np.allclose(z.imag, 1.1999 * 0.1 * np.sin(th))
+    # w_j is dz/dtheta / (i rho): the trapezoid weight of (1/2 pi i) contour integral
+    dz = 1.1999 * (-np.sin(th) + 1j * 0.1 * np.cos(th))
+    assert np.allclose(w, dz / (1j * 1.1999))
+
+
+def test_conjugate_symmetry_makes_r_real():
+    z, c, c0 = contour.single_contour(64, 3.3, 3.3, 0.28)
+    assert np.allclose(z[::-1], z.conj()) and np.allclose(c[::-1], c.conj())
+    lam = np.linspace(-7, 7, 301)
+    assert np.abs(contour.rational(lam, z, c, c0).imag).max() < 1e-13
+
+
+def test_residue_theorem_limit():
+    """As N grows the rule converges to the indicator of the enclosed region."""
+    z, p = contour.projector_coefficients(400, 1.2, 1.1999, 0.1)
+    inside = contour.rational(np.array([0.05, 1.0, 2.3]), z, p, 0.0)
+    outside = contour.rational(np.array([-0.05, -1.0, 2.5]), z, p, 0.0)
+    assert np.abs(inside - 1).max() < 1e-9
+    assert np.abs(outside).max() < 1e-9
+
+
+def test_paper_contour_accuracy():
+    """With the paper's setup (alpha = 0.1, rho = 1.1999, gamma = +-1.2) and 500 nodes
+    per contour the sign function is reproduced to ~1e-14 on +-[0.01, 2]; 250 nodes
+    leave ~1e-7.  This is the scalar content of the sigma-vs-N behaviour the paper reports."""
+    lam = np.concatenate([np.linspace(0.01, 2.0, 400), -np.linspace(0.01, 2.0, 400)])
+    z, c, c0 = contour.paper_two_contour(500)
+    e500 = np.abs(contour.rational(lam, z, c, c0) - np.sign(lam)).max()
+    z, c, c0 = contour.paper_two_contour(250)
+    e250 = np.abs(contour.rational(lam, z, c, c0) - np.sign(lam)).max()
+    assert e500 < 5e-14
+    assert 1e-9 < e250 < 1e-5
+
+
+def test_single_contour_is_twice_projector_minus_one():
+    z, c, c0 = contour.single_contour(48, 2.0, 2.0, 0.3)
+    zp, p = contour.projector_coefficients(48, 2.0, 2.0, 0.3)
+    lam = np.array([-1.0, 0.5, 3.0])
+    assert np.allclose(contour.rational(lam, z, c, c0), 2 * contour.rational(lam, zp, p, 0.0) - 1)
