@@ -1,0 +1,198 @@
+/*
+ * ov.h -- C ABI of the GB300 (sm_103a) contour-integral overlap library.
+ *
+ * The library computes, on one GPU,
+ *
+ *   sgn(H_W) b  ~=  S_N b = c0 b + sum_{j=1..N} c_j (z_j - H_W)^-1 b      (Eqs. 5-7)
+ *   D_ov(m_q) b  =  (1 + m_q)/2 b + (1 - m_q)/2 gamma5 S_N b              (Eq. 1)
+ *
+ * for the hermitian Wilson-Dirac operator H_W = gamma5 D_W(-m0) (Eq. 1 and the
+ * definition of H_W after it) on a 4D periodic lattice with SU(3) links, where
+ * the nodes z_j and coefficients c_j come from the N-point trapezoid rule on an
+ * ellipse (Eq. 7).  The resolvents (z_j - H_W)^-1 b of Eq. 6 are produced by one
+ * shifted Krylov solve for all nodes at once (the shift-solver remark after
+ * Eq. 7).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * dims = {Lx, Ly, Lz, Lt}; direction mu = 0,1,2,3 is x,y,z,t.
+ * D_W psi(x) = (4r + m) psi(x) - 1/2 sum_mu [ (r - g_mu) U_mu(x) psi(x+mu)
+ *                                            + (r + g_mu) U_mu(x-mu)^dag psi(x-mu) ],
+ * m = -m0; r must be 1.  Space is periodic; time is periodic (bc_t = +1) or
+ * antiperiodic (bc_t = -1, a sign on every hop across the t boundary).
+ * Chiral basis: g_k = [[0, -i s_k], [i s_k, 0]] (k = x, y, z), g_t = [[0, 1], [1, 0]],
+ * gamma5 = g_x g_y g_z g_t = diag(1, 1, -1, -1).
+ *
+ * Canonical layouts (all complex numbers interleaved re, im; x fastest):
+ *   gauge field  U[mu][t][z][y][x][row 3][col 3]                 complex double
+ *   spinor       psi[rhs][t][z][y][x][spin 4][colour 3]          complex double or float
+ *   link force   F[mu][t][z][y][x][a 8]                          double (real)
+ * V = Lx*Ly*Lz*Lt sites; one spinor is 12 V complex numbers.
+ *
+ * Ownership and streams: every vector argument is a pointer the caller owns and
+ * keeps alive until the work enqueued on `stream` has finished.  Pointers are
+ * DEVICE pointers unless the entry point or an option says otherwise.  `stream`
+ * is a cudaStream_t passed as void* (NULL = the legacy default stream).  The
+ * context owns its gauge copies, contour and workspace; workspace grows on
+ * demand and is reused.  A context is not thread safe: serialise calls on it.
+ *
+ * Errors: every entry point returns an ov_status.  Nothing aborts, traps or
+ * spins without bound on the device: every device loop has an iteration limit
+ * and reports through the status.  ov_last_error() gives a one-line reason.
+ */
+#ifndef OV_H_
+#define OV_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ov_ctx ov_ctx;
+
+typedef enum {
+  OV_OK = 0,
+  OV_ERR_INVALID_ARG = 1,   /* bad pointer, size, flag or parameter            */
+  OV_ERR_OUT_OF_MEMORY = 2, /* device allocation failed                        */
+  OV_ERR_NOT_CONVERGED = 3, /* iteration limit hit; output holds the last iterate */
+  OV_ERR_BREAKDOWN = 4,     /* a Krylov recurrence produced a non-finite scalar */
+  OV_ERR_CUDA = 5,          /* a CUDA runtime call failed                      */
+  OV_ERR_NO_GAUGE = 6,      /* ov_set_gauge has not been called                */
+  OV_ERR_NO_CONTOUR = 7     /* no contour set on the context                   */
+} ov_status;
+
+typedef enum { OV_FP64 = 0, OV_FP32 = 1 } ov_precision;
+
+/* Solver modes for ov_sgn_HW_apply / ov_overlap_apply / ov_sgn_vjp. */
+typedef enum {
+  /* FP64 shifted solve: one Lanczos process on H_W serves every node; each node
+   * keeps its own FP64 search direction and the weighted sum of Eq. 7 is
+   * accumulated in the same pass (the paper's shift-solver structure). */
+  OV_MODE_FP64 = 0,
+  /* Mixed precision: FP32 shifted solve, then batched per-node FP64 true
+   * residuals and FP32 defect-correction solves over all nodes x sources in
+   * one multi-RHS launch, FP64 quadrature sum. */
+  OV_MODE_MIXED = 1,
+  /* FP64 two-pass Lanczos: the per-node recurrences of OV_MODE_FP64 are carried
+   * out on the tridiagonal Lanczos matrix instead of on vectors; a second
+   * Lanczos pass rebuilds the basis and accumulates the sum.  Same result,
+   * vector work independent of the number of nodes. */
+  OV_MODE_FP64_2PASS = 2
+} ov_mode;
+
+typedef enum {
+  OV_CONTOUR_SINGLE = 0, /* sgn = 2 P_Gamma - 1, one ellipse around the positive spectrum */
+  OV_CONTOUR_PAIR = 1    /* sgn = P_{Gamma+} - P_{Gamma-} (Eqs. 3, 5), centres +gamma and -gamma */
+} ov_contour_form;
+
+/* Options for the solves (pass NULL for the defaults in brackets). */
+typedef struct {
+  int mode;         /* ov_mode                                              [OV_MODE_FP64] */
+  double tol;       /* per-node relative residual ||b - (z_j - H) y_j|| / ||b||   [1e-12] */
+  int max_iter;     /* Krylov iteration limit per solve                          [20000] */
+  int host_io;      /* 1: b / out / eta / grad_b are HOST pointers; copies to and
+                       from the device are enqueued on `stream` inside the call  [0] */
+  int check_every;  /* iterations between host reads of the convergence flag  [32] */
+  int use_graph;    /* 1: replay the per-iteration kernels from a CUDA graph     [1] */
+} ov_solve_opts;
+
+/* Per-call statistics (optional output, may be NULL). */
+typedef struct {
+  int iterations;        /* Krylov iterations of the (outer) solve, max over sources       */
+  int refine_rounds;     /* OV_MODE_MIXED: defect-correction rounds                          */
+  int inner_iterations;  /* OV_MODE_MIXED: total iterations of the correction solves          */
+  int converged;         /* 1 if every node of every source met tol                           */
+  double max_residual;   /* max over nodes and sources of the final relative residual          */
+  double error_bound;    /* max over sources of sum_j |c_j| r_j / |Im z_j| (relative to ||b||):
+                            bound on ||S_N b - out|| / ||b|| because ||(z - H)^-1|| <= 1/|Im z| */
+  double ms;             /* wall time of the call on the host, milliseconds                  */
+} ov_stats;
+
+/* Spectral bounds from Lanczos (ov_place_contour). */
+typedef struct {
+  double lambda_min;     /* smallest Ritz value of H_W                                 */
+  double lambda_max;     /* largest Ritz value of H_W                                   */
+  double abs_max_bound;  /* upper bound on max |lambda| (Ritz value + residual bound)    */
+  double gap;            /* estimate of min |lambda| (sqrt of the smallest Ritz value of H_W^2) */
+  double predicted_error;/* max |r_N(lambda) - sgn(lambda)| over +-[gap, abs_max_bound] */
+  double gamma, rho, alpha; /* the ellipse chosen                                       */
+  int steps;             /* Lanczos steps taken                                          */
+} ov_spectrum;
+
+/* Create a context on CUDA device `device` for a lattice of size dims.
+ * bc_t: +1 periodic, -1 antiperiodic time.  r must be 1.0.
+ * Errors: INVALID_ARG (dims < 1, |bc_t| != 1, r != 1), CUDA, OUT_OF_MEMORY. */
+int ov_create(ov_ctx** ctx, const int dims[4], int bc_t, double m0, double r, int device);
+
+/* Release every device and host resource of the context (NULL is accepted). */
+int ov_destroy(ov_ctx* ctx);
+
+/* One-line description of the last error on this context (never NULL). */
+const char* ov_last_error(const ov_ctx* ctx);
+
+/* Load the gauge field (canonical layout, V*4*9 complex doubles).  U may be a
+ * host (on_device = 0) or device (on_device = 1) pointer; it is not retained.
+ * The library keeps FP64 and FP32 structure-of-arrays copies.  Any cached
+ * contour placement is invalidated (explicit contours are kept). */
+int ov_set_gauge(ov_ctx* ctx, const double* U, int on_device, void* stream);
+
+/* out = H_W in for nrhs spinors in the canonical layout, in the given precision
+ * (OV_FP64: complex double, OV_FP32: complex float).  in and out must not alias. */
+int ov_apply_HW(ov_ctx* ctx, const void* in, void* out, int nrhs, int precision, void* stream);
+
+/* Set an explicit quadrature: S_N = c0 + sum_j c_j (z_j - H)^-1.  z and c point
+ * to n interleaved complex doubles on the host; every Im z_j must be nonzero. */
+int ov_set_contour(ov_ctx* ctx, int n, const double* z, const double* c, double c0_re, double c0_im);
+
+/* Set the trapezoid rule of Eq. 7 on the ellipse z = gamma + rho (cos t + i alpha sin t),
+ * theta_j = 2 pi (j - 1/2) / n_q.  OV_CONTOUR_SINGLE: c_j = 2 rho w_j / n_q, c0 = -1
+ * (n_q nodes).  OV_CONTOUR_PAIR: c_j = +-rho w_j / n_q on the ellipses centred at
+ * +-gamma, c0 = 0 (2 n_q nodes). */
+int ov_set_contour_ellipse(ov_ctx* ctx, int n_q, double gamma, double rho, double alpha, int form);
+
+/* Copy the current quadrature to host arrays (z, c: room for *n complex doubles;
+ * on return *n is the node count).  Pass z = c = NULL to query the count. */
+int ov_get_contour(const ov_ctx* ctx, int* n, double* z, double* c, double* c0);
+
+/* Choose a single-contour ellipse of n_q nodes from Lanczos bounds of H_W and H_W^2
+ * (`steps` Lanczos steps on each, from a fixed pseudo-random start) and set it on
+ * the context.  The ellipse crosses the real axis at 0 and just beyond the upper
+ * bound of the spectrum; alpha minimises the predicted method error.  `out` may be NULL. */
+int ov_place_contour(ov_ctx* ctx, int n_q, int steps, ov_spectrum* out, void* stream);
+
+/* out = S_N b for nrhs sources (complex double, canonical layout). */
+int ov_sgn_HW_apply(ov_ctx* ctx, const void* b, void* out, int nrhs, const ov_solve_opts* opts,
+                    ov_stats* stats, void* stream);
+
+/* out = D_ov(m_q) b = (1 + m_q)/2 b + (1 - m_q)/2 gamma5 S_N b (Eq. 1). */
+int ov_overlap_apply(ov_ctx* ctx, double m_q, const void* b, void* out, int nrhs,
+                     const ov_solve_opts* opts, ov_stats* stats, void* stream);
+
+/* Gradients of L = Re <eta, S_N b> (one source):
+ *   grad_b     = S_N^dag eta (complex double spinor): dL = Re <grad_b, db>;
+ *   grad_links = dL/d omega_{x,mu,a} for U_mu(x) -> exp(i omega_a lambda_a/2) U_mu(x)
+ *                (double [mu][t][z][y][x][8]).
+ * Either output may be NULL.  Per-node forward y_j and adjoint (conj(z_j) - H)^-1 eta
+ * solutions are kept in device memory during the call. */
+int ov_sgn_vjp(ov_ctx* ctx, const void* eta, const void* b, void* grad_b, double* grad_links,
+               const ov_solve_opts* opts, ov_stats* stats, void* stream);
+
+/* Gradients of L = Re <eta, D_ov(m_q) b>: grad_b = (1+m_q)/2 eta + (1-m_q)/2 S_N^dag gamma5 eta,
+ * grad_links = (1-m_q)/2 times the force of ov_sgn_vjp with eta -> gamma5 eta. */
+int ov_overlap_vjp(ov_ctx* ctx, double m_q, const void* eta, const void* b, void* grad_b,
+                   double* grad_links, const ov_solve_opts* opts, ov_stats* stats, void* stream);
+
+/* Kernel timing: when enabled, the library brackets every launch of its main
+ * kernel classes with CUDA events on the launching stream and accumulates their
+ * durations.  ov_kernel_times fills up to `cap` entries (name pointer, launches,
+ * total ms) and returns the number of classes.  Disabled by default. */
+int ov_set_kernel_timing(ov_ctx* ctx, int enable);
+int ov_kernel_times(ov_ctx* ctx, const char** names, long long* launches, double* total_ms, int cap);
+
+/* Library version string. */
+const char* ov_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OV_H_ */

@@ -1,0 +1,504 @@
+// The C ABI entry points declared in include/ov.h, and the context utilities.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+const char* const kKernelClassNames[KC_COUNT] = {"hw_kernel",         "lanczos_hw_kernel", "lanczos_update_kernel",
+                                                  "layout_kernels",    "init_kernels",      "force_kernel",
+                                                  "residual_kernels"};
+
+// ------------------------------------------------------------ utilities
+
+int ctx_fail(ov_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int ctx_cuda(ov_ctx* ctx, cudaError_t e, const char* what) {
+  return ctx_fail(ctx, e == cudaErrorMemoryAllocation ? OV_ERR_OUT_OF_MEMORY : OV_ERR_CUDA,
+                  std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void* ws_get(ov_ctx* ctx, const char* name, size_t bytes, int* status) {
+  if (*status != OV_OK) return nullptr;
+  DevBuf& b = ctx->bufs[name];
+  if (b.bytes >= bytes && b.p) return b.p;
+  if (b.p) {
+    cudaDeviceSynchronize();
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    graphs_release(ctx);  // captured graphs may point at the old buffer
+  }
+  const size_t nb = std::max<size_t>(bytes, 256);
+  cudaError_t e = cudaMalloc(&b.p, nb);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    *status = ctx_fail(ctx, OV_ERR_OUT_OF_MEMORY,
+                       std::string("cudaMalloc of workspace '") + name + "' (" + std::to_string(nb) + " bytes) failed");
+    return nullptr;
+  }
+  b.bytes = nb;
+  return b.p;
+}
+
+void ws_release_all(ov_ctx* ctx) {
+  for (auto& kv : ctx->bufs)
+    if (kv.second.p) cudaFree(kv.second.p);
+  ctx->bufs.clear();
+}
+
+void graphs_release(ov_ctx* ctx) {
+  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  ctx->graphs.clear();
+}
+
+void kt_begin(ov_ctx* ctx, int cls, cudaStream_t s, cudaEvent_t* a) {
+  *a = nullptr;
+  if (!ctx->timing) return;
+  if (ctx->event_pool.empty()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    ctx->event_pool.push_back(e);
+  }
+  *a = ctx->event_pool.back();
+  ctx->event_pool.pop_back();
+  cudaEventRecord(*a, s);
+  (void)cls;
+}
+
+void kt_end(ov_ctx* ctx, int cls, cudaStream_t s, cudaEvent_t a) {
+  if (!ctx->timing || !a) return;
+  cudaEvent_t b;
+  if (ctx->event_pool.empty()) {
+    if (cudaEventCreate(&b) != cudaSuccess) return;
+  } else {
+    b = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+  }
+  cudaEventRecord(b, s);
+  ctx->pending.push_back({cls, a, b});
+}
+
+void kt_collect(ov_ctx* ctx) {
+  for (auto& p : ctx->pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      ctx->clocks[p.cls].launches += 1;
+      ctx->clocks[p.cls].total_ms += ms;
+    }
+    ctx->event_pool.push_back(p.a);
+    ctx->event_pool.push_back(p.b);
+  }
+  ctx->pending.clear();
+}
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+ov_solve_opts resolve_opts(const ov_solve_opts* o) {
+  ov_solve_opts r;
+  r.mode = OV_MODE_FP64;
+  r.tol = 1e-12;
+  r.max_iter = 20000;
+  r.host_io = 0;
+  r.check_every = 32;
+  r.use_graph = 1;
+  if (o) r = *o;
+  if (r.check_every <= 0) r.check_every = 32;
+  return r;
+}
+
+int check_opts(ov_ctx* ctx, const ov_solve_opts& o) {
+  if (!(o.tol > 0.0) || !(o.tol < 1.0)) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "tol must be in (0, 1)");
+  if (o.max_iter < 1) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "max_iter must be >= 1");
+  if (o.mode != OV_MODE_FP64 && o.mode != OV_MODE_MIXED && o.mode != OV_MODE_FP64_2PASS)
+    return ctx_fail(ctx, OV_ERR_INVALID_ARG, "unknown solver mode");
+  return OV_OK;
+}
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Device copy of a (possibly host) canonical spinor set; returns the device pointer.
+const double2* stage_in(ov_ctx* ctx, const void* p, size_t bytes, int host_io, const char* name, cudaStream_t s,
+                        int* st) {
+  if (!host_io) return (const double2*)p;
+  void* d = ws_get(ctx, name, bytes, st);
+  if (*st != OV_OK) return nullptr;
+  cudaError_t e = cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) *st = ctx_cuda(ctx, e, "host-to-device copy");
+  return (const double2*)d;
+}
+
+// Core of sgn / overlap: canonical b (device) -> S_N b (SoA, workspace).
+int sign_core(ov_ctx* ctx, const double2* b_dev, int nrhs, const ov_solve_opts& o, SolveOut* so, cudaStream_t s,
+              double2** s_soa_out, double2* xs) {
+  int st = OV_OK;
+  const size_t n = (size_t)12 * ctx->g.V * nrhs;
+  double2* b_soa = (double2*)ws_get(ctx, "api.b_soa", sizeof(double2) * n, &st);
+  double2* s_soa = (double2*)ws_get(ctx, "api.s_soa", sizeof(double2) * n, &st);
+  if (st != OV_OK) return st;
+  st = launch_pack64(ctx, b_dev, b_soa, nrhs, s);
+  if (st != OV_OK) return st;
+  if (o.mode == OV_MODE_FP64) {
+    st = solve_sign_soa(ctx, b_soa, s_soa, nrhs, o, so, s, xs);
+  } else {
+    return ctx_fail(ctx, OV_ERR_INVALID_ARG, "solver mode not available in this build");
+  }
+  *s_soa_out = s_soa;
+  return st;
+}
+
+void fill_stats(ov_stats* st, const SolveOut& so, double ms) {
+  if (!st) return;
+  st->iterations = so.iterations;
+  st->refine_rounds = so.refine_rounds;
+  st->inner_iterations = so.inner_iterations;
+  st->converged = so.converged;
+  st->max_residual = so.max_residual;
+  st->error_bound = so.error_bound;
+  st->ms = ms;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ ABI
+
+extern "C" {
+
+const char* ov_version(void) { return "ov-gb300 0.1 (sm_103a)"; }
+
+int ov_create(ov_ctx** out, const int dims[4], int bc_t, double m0, double r, int device) {
+  if (!out || !dims) return OV_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int k = 0; k < 4; ++k)
+    if (dims[k] < 1) return OV_ERR_INVALID_ARG;
+  if (bc_t != 1 && bc_t != -1) return OV_ERR_INVALID_ARG;
+  if (r != 1.0) return OV_ERR_INVALID_ARG;
+  if (!std::isfinite(m0)) return OV_ERR_INVALID_ARG;
+  const long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+  if (V > (1LL << 28)) return OV_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return OV_ERR_CUDA;
+  }
+  ov_ctx* ctx = new ov_ctx();
+  ctx->device = device;
+  DeviceGuard dg(device);
+  for (int k = 0; k < 4; ++k) ctx->g.L[k] = dims[k];
+  ctx->g.st[0] = 1;
+  ctx->g.st[1] = dims[0];
+  ctx->g.st[2] = dims[0] * dims[1];
+  ctx->g.st[3] = dims[0] * dims[1] * dims[2];
+  ctx->g.V = (int)V;
+  ctx->g.bc_t = bc_t;
+  ctx->m0 = m0;
+  ctx->r = r;
+  if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaHostAlloc((void**)&ctx->host_flag, sizeof(int) * 4, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    ov_destroy(ctx);
+    return OV_ERR_CUDA;
+  }
+  *out = ctx;
+  return OV_OK;
+}
+
+int ov_destroy(ov_ctx* ctx) {
+  if (!ctx) return OV_OK;
+  DeviceGuard dg(ctx->device);
+  cudaDeviceSynchronize();
+  graphs_release(ctx);
+  ws_release_all(ctx);
+  if (ctx->U64) cudaFree(ctx->U64);
+  if (ctx->U32) cudaFree(ctx->U32);
+  for (auto& p : ctx->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : ctx->event_pool) cudaEventDestroy(e);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->host_flag) cudaFreeHost(ctx->host_flag);
+  delete ctx;
+  return OV_OK;
+}
+
+const char* ov_last_error(const ov_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int ov_set_gauge(ov_ctx* ctx, const double* U, int on_device, void* stream) {
+  if (!ctx) return OV_ERR_INVALID_ARG;
+  if (!U) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "null gauge pointer");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)4 * ctx->g.V * 9;
+  if (!ctx->U64) {
+    if (cudaMalloc(&ctx->U64, sizeof(double2) * n) != cudaSuccess ||
+        cudaMalloc(&ctx->U32, sizeof(float2) * n) != cudaSuccess) {
+      cudaGetLastError();
+      return ctx_fail(ctx, OV_ERR_OUT_OF_MEMORY, "gauge field allocation failed");
+    }
+  }
+  int st = OV_OK;
+  const double2* src = (const double2*)U;
+  if (!on_device) {
+    double2* tmp = (double2*)ws_get(ctx, "gauge.stage", sizeof(double2) * n, &st);
+    if (st != OV_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(tmp, U, sizeof(double2) * n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "gauge copy");
+    src = tmp;
+  }
+  st = launch_gauge_ingest(ctx, src, s);
+  if (st != OV_OK) return st;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "ov_set_gauge");
+  kt_collect(ctx);
+  ctx->have_gauge = true;
+  return OV_OK;
+}
+
+int ov_apply_HW(ov_ctx* ctx, const void* in, void* out, int nrhs, int precision, void* stream) {
+  if (!ctx) return OV_ERR_INVALID_ARG;
+  if (!ctx->have_gauge) return ctx_fail(ctx, OV_ERR_NO_GAUGE, "ov_set_gauge has not been called");
+  if (nrhs < 0 || (nrhs > 0 && (!in || !out)) || in == out)
+    return ctx_fail(ctx, OV_ERR_INVALID_ARG, "bad vectors for ov_apply_HW");
+  if (precision != OV_FP64 && precision != OV_FP32) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "bad precision");
+  if (nrhs == 0) return OV_OK;
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)12 * ctx->g.V * nrhs;
+  int st = OV_OK;
+  if (precision == OV_FP64) {
+    double2* a = (double2*)ws_get(ctx, "hw.a64", sizeof(double2) * n, &st);
+    double2* b = (double2*)ws_get(ctx, "hw.b64", sizeof(double2) * n, &st);
+    if (st != OV_OK) return st;
+    if ((st = launch_pack64(ctx, (const double2*)in, a, nrhs, s))) return st;
+    if ((st = launch_hw64(ctx, a, b, nrhs, s))) return st;
+    if ((st = launch_unpack64(ctx, b, (double2*)out, nrhs, s))) return st;
+  } else {
+    float2* a = (float2*)ws_get(ctx, "hw.a32", sizeof(float2) * n, &st);
+    float2* b = (float2*)ws_get(ctx, "hw.b32", sizeof(float2) * n, &st);
+    if (st != OV_OK) return st;
+    if ((st = launch_pack32(ctx, (const float2*)in, a, nrhs, s))) return st;
+    if ((st = launch_hw32(ctx, a, b, nrhs, s))) return st;
+    if ((st = launch_unpack32(ctx, b, (float2*)out, nrhs, s))) return st;
+  }
+  return OV_OK;
+}
+
+int ov_set_contour(ov_ctx* ctx, int n, const double* z, const double* c, double c0_re, double c0_im) {
+  if (!ctx) return OV_ERR_INVALID_ARG;
+  if (n < 1 || !z || !c) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "bad contour arrays");
+  std::vector<double2> zz(n), cc(n);
+  for (int j = 0; j < n; ++j) {
+    zz[j] = make_double2(z[2 * j], z[2 * j + 1]);
+    cc[j] = make_double2(c[2 * j], c[2 * j + 1]);
+    if (!std::isfinite(zz[j].x) || !std::isfinite(zz[j].y) || !std::isfinite(cc[j].x) || !std::isfinite(cc[j].y))
+      return ctx_fail(ctx, OV_ERR_INVALID_ARG, "non-finite node or coefficient");
+    if (zz[j].y == 0.0) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "a node lies on the real axis");
+  }
+  ctx->z = zz;
+  ctx->c = cc;
+  ctx->c0 = make_double2(c0_re, c0_im);
+  ctx->have_contour = true;
+  return OV_OK;
+}
+
+int ov_set_contour_ellipse(ov_ctx* ctx, int n_q, double gamma, double rho, double alpha, int form) {
+  if (!ctx) return OV_ERR_INVALID_ARG;
+  if (n_q < 1 || !(rho > 0) || !(alpha > 0) || !std::isfinite(gamma) ||
+      (form != OV_CONTOUR_SINGLE && form != OV_CONTOUR_PAIR))
+    return ctx_fail(ctx, OV_ERR_INVALID_ARG, "bad ellipse parameters");
+  std::vector<double2> z, c;
+  double2 c0;
+  ellipse_rule(n_q, gamma, rho, alpha, form, z, c, c0);
+  for (auto& zz : z)
+    if (zz.y == 0.0) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "a node lies on the real axis");
+  ctx->z = z;
+  ctx->c = c;
+  ctx->c0 = c0;
+  ctx->have_contour = true;
+  return OV_OK;
+}
+
+int ov_get_contour(const ov_ctx* ctx, int* n, double* z, double* c, double* c0) {
+  if (!ctx || !n) return OV_ERR_INVALID_ARG;
+  if (!ctx->have_contour) return OV_ERR_NO_CONTOUR;
+  const int nn = (int)ctx->z.size();
+  if (z && c) {
+    if (*n < nn) return OV_ERR_INVALID_ARG;
+    for (int j = 0; j < nn; ++j) {
+      z[2 * j] = ctx->z[j].x;
+      z[2 * j + 1] = ctx->z[j].y;
+      c[2 * j] = ctx->c[j].x;
+      c[2 * j + 1] = ctx->c[j].y;
+    }
+  }
+  if (c0) {
+    c0[0] = ctx->c0.x;
+    c0[1] = ctx->c0.y;
+  }
+  *n = nn;
+  return OV_OK;
+}
+
+int ov_place_contour(ov_ctx* ctx, int n_q, int steps, ov_spectrum* out, void* stream) {
+  if (!ctx) return OV_ERR_INVALID_ARG;
+  if (!ctx->have_gauge) return ctx_fail(ctx, OV_ERR_NO_GAUGE, "ov_set_gauge has not been called");
+  if (n_q < 2 || steps < 4) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "need n_q >= 2 and steps >= 4");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<double> a, b;
+  int st = lanczos_tridiag(ctx, steps, 0, a, b, s);
+  if (st != OV_OK) return st;
+  double lo, hi, rlo, rhi;
+  tridiag_extreme_eigs(a, b, &lo, &hi, &rlo, &rhi);
+  const double amax = std::max(std::fabs(lo) + rlo, std::fabs(hi) + rhi);
+  std::vector<double> a2, b2;
+  st = lanczos_tridiag(ctx, steps, 1, a2, b2, s);
+  if (st != OV_OK) return st;
+  double lo2, hi2, rlo2, rhi2;
+  tridiag_extreme_eigs(a2, b2, &lo2, &hi2, &rlo2, &rhi2);
+  double gap = std::sqrt(std::max(lo2, 0.0));
+  gap = std::max(gap, 1e-6 * amax);
+  // single ellipse from 0 to 1.05 * amax; alpha minimises the predicted method error
+  const double R = 1.05 * amax;
+  const double gam = 0.5 * R, rho = 0.5 * R;
+  std::vector<double> lam;
+  const int nl = 200;
+  for (int k = 0; k < nl; ++k) {
+    const double t = (double)k / (nl - 1);
+    const double l = gap * std::pow(amax / gap, t);
+    lam.push_back(l);
+    lam.push_back(-l);
+  }
+  double best_err = 1e300, best_alpha = 0.1;
+  std::vector<double2> z, c;
+  double2 c0;
+  for (int k = 0; k <= 190; ++k) {
+    const double al = 0.05 + 0.005 * k;
+    ellipse_rule(n_q, gam, rho, al, OV_CONTOUR_SINGLE, z, c, c0);
+    double err = 0.0;
+    for (double l : lam) err = std::max(err, std::fabs(rational_value(l, z, c, c0) - (l > 0 ? 1.0 : -1.0)));
+    if (err < best_err) {
+      best_err = err;
+      best_alpha = al;
+    }
+  }
+  st = ov_set_contour_ellipse(ctx, n_q, gam, rho, best_alpha, OV_CONTOUR_SINGLE);
+  if (st != OV_OK) return st;
+  if (out) {
+    out->lambda_min = lo;
+    out->lambda_max = hi;
+    out->abs_max_bound = amax;
+    out->gap = gap;
+    out->predicted_error = best_err;
+    out->gamma = gam;
+    out->rho = rho;
+    out->alpha = best_alpha;
+    out->steps = (int)a.size();
+  }
+  return OV_OK;
+}
+
+static int sign_or_overlap(ov_ctx* ctx, bool overlap, double m_q, const void* b, void* out, int nrhs,
+                           const ov_solve_opts* opts, ov_stats* stats, void* stream) {
+  const double t0 = now_ms();
+  if (!ctx) return OV_ERR_INVALID_ARG;
+  if (!ctx->have_gauge) return ctx_fail(ctx, OV_ERR_NO_GAUGE, "ov_set_gauge has not been called");
+  if (!ctx->have_contour) return ctx_fail(ctx, OV_ERR_NO_CONTOUR, "no contour set");
+  if (nrhs < 0 || (nrhs > 0 && (!b || !out))) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "bad vectors");
+  if (!std::isfinite(m_q)) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "m_q is not finite");
+  ov_solve_opts o = resolve_opts(opts);
+  int st = check_opts(ctx, o);
+  if (st != OV_OK) return st;
+  if (nrhs == 0) return OV_OK;
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)12 * ctx->g.V * nrhs;
+  const double2* bd = stage_in(ctx, b, sizeof(double2) * n, o.host_io, "io.b", s, &st);
+  if (st != OV_OK) return st;
+  double2* od = o.host_io ? (double2*)ws_get(ctx, "io.out", sizeof(double2) * n, &st) : (double2*)out;
+  if (st != OV_OK) return st;
+  SolveOut so;
+  double2* s_soa = nullptr;
+  const int sst = sign_core(ctx, bd, nrhs, o, &so, s, &s_soa, nullptr);
+  if (sst != OV_OK && sst != OV_ERR_NOT_CONVERGED) return sst;
+  if (overlap)
+    st = launch_overlap_epilogue(ctx, bd, s_soa, od, m_q, nrhs, s);
+  else
+    st = launch_unpack64(ctx, s_soa, od, nrhs, s);
+  if (st != OV_OK) return st;
+  if (o.host_io) {
+    cudaError_t e = cudaMemcpyAsync(out, od, sizeof(double2) * n, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "device-to-host copy");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "sync");
+  }
+  kt_collect(ctx);
+  fill_stats(stats, so, now_ms() - t0);
+  return sst;
+}
+
+int ov_sgn_HW_apply(ov_ctx* ctx, const void* b, void* out, int nrhs, const ov_solve_opts* opts, ov_stats* stats,
+                    void* stream) {
+  return sign_or_overlap(ctx, false, 0.0, b, out, nrhs, opts, stats, stream);
+}
+
+int ov_overlap_apply(ov_ctx* ctx, double m_q, const void* b, void* out, int nrhs, const ov_solve_opts* opts,
+                     ov_stats* stats, void* stream) {
+  return sign_or_overlap(ctx, true, m_q, b, out, nrhs, opts, stats, stream);
+}
+
+int ov_sgn_vjp(ov_ctx* ctx, const void* eta, const void* b, void* grad_b, double* grad_links,
+               const ov_solve_opts* opts, ov_stats* stats, void* stream) {
+  (void)eta; (void)b; (void)grad_b; (void)grad_links; (void)opts; (void)stats; (void)stream;
+  return ctx_fail(ctx, OV_ERR_INVALID_ARG, "ov_sgn_vjp is not available in this build");
+}
+
+int ov_overlap_vjp(ov_ctx* ctx, double m_q, const void* eta, const void* b, void* grad_b, double* grad_links,
+                   const ov_solve_opts* opts, ov_stats* stats, void* stream) {
+  (void)m_q; (void)eta; (void)b; (void)grad_b; (void)grad_links; (void)opts; (void)stats; (void)stream;
+  return ctx_fail(ctx, OV_ERR_INVALID_ARG, "ov_overlap_vjp is not available in this build");
+}
+
+int ov_set_kernel_timing(ov_ctx* ctx, int enable) {
+  if (!ctx) return OV_ERR_INVALID_ARG;
+  kt_collect(ctx);
+  ctx->timing = enable != 0;
+  for (auto& c : ctx->clocks) c = KernelClock{};
+  return OV_OK;
+}
+
+int ov_kernel_times(ov_ctx* ctx, const char** names, long long* launches, double* total_ms, int cap) {
+  if (!ctx) return OV_ERR_INVALID_ARG;
+  kt_collect(ctx);
+  for (int k = 0; k < KC_COUNT && k < cap; ++k) {
+    if (names) names[k] = kKernelClassNames[k];
+    if (launches) launches[k] = ctx->clocks[k].launches;
+    if (total_ms) total_ms[k] = ctx->clocks[k].total_ms;
+  }
+  return KC_COUNT;
+}
+
+}  // extern "C"

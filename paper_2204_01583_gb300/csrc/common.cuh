@@ -1,0 +1,203 @@
+// Device helpers shared by the library's kernels: complex arithmetic, lattice
+// neighbours, the Wilson stencil at one site and deterministic block reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ov_internal.h"
+
+template <typename R>
+struct Cx {
+  R re, im;
+};
+
+template <typename R> struct Store;
+template <> struct Store<double> { using T = double2; };
+template <> struct Store<float> { using T = float2; };
+
+template <typename R>
+__device__ __forceinline__ Cx<R> ld(const typename Store<R>::T* p) {
+  typename Store<R>::T v = __ldg(p);
+  return {v.x, v.y};
+}
+template <typename R>
+__device__ __forceinline__ void st(typename Store<R>::T* p, Cx<R> v) {
+  typename Store<R>::T w;
+  w.x = v.re;
+  w.y = v.im;
+  *p = w;
+}
+
+template <typename R> __device__ __forceinline__ Cx<R> cadd(Cx<R> a, Cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R> __device__ __forceinline__ Cx<R> csub(Cx<R> a, Cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R> __device__ __forceinline__ Cx<R> cscale(R s, Cx<R> a) { return {s * a.re, s * a.im}; }
+// i * a and -i * a
+template <typename R> __device__ __forceinline__ Cx<R> cmuli(Cx<R> a) { return {-a.im, a.re}; }
+template <typename R> __device__ __forceinline__ Cx<R> cmulmi(Cx<R> a) { return {a.im, -a.re}; }
+template <typename R> __device__ __forceinline__ Cx<R> cneg(Cx<R> a) { return {-a.re, -a.im}; }
+// acc + a * b
+template <typename R>
+__device__ __forceinline__ Cx<R> cfma(Cx<R> a, Cx<R> b, Cx<R> acc) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+  return acc;
+}
+// acc + conj(a) * b
+template <typename R>
+__device__ __forceinline__ Cx<R> cfmaconj(Cx<R> a, Cx<R> b, Cx<R> acc) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+  return acc;
+}
+template <typename R> __device__ __forceinline__ R cnorm2(Cx<R> a) { return a.re * a.re + a.im * a.im; }
+
+// ------------------------------------------------------------ neighbours
+
+__device__ __forceinline__ void site_coords(const Geom& g, int s, int c[4]) {
+  c[0] = s % g.L[0];
+  int q = s / g.L[0];
+  c[1] = q % g.L[1];
+  q /= g.L[1];
+  c[2] = q % g.L[2];
+  c[3] = q / g.L[2];
+}
+
+// site index of x + mu (fwd) or x - mu (bwd) and the boundary sign of that hop
+__device__ __forceinline__ int nb_fwd(const Geom& g, int s, const int c[4], int mu, int* sgn) {
+  if (c[mu] + 1 == g.L[mu]) {
+    *sgn = (mu == 3) ? g.bc_t : 1;
+    return s - (g.L[mu] - 1) * g.st[mu];
+  }
+  *sgn = 1;
+  return s + g.st[mu];
+}
+__device__ __forceinline__ int nb_bwd(const Geom& g, int s, const int c[4], int mu, int* sgn) {
+  if (c[mu] == 0) {
+    *sgn = (mu == 3) ? g.bc_t : 1;
+    return s + (g.L[mu] - 1) * g.st[mu];
+  }
+  *sgn = 1;
+  return s - g.st[mu];
+}
+
+// ------------------------------------------------------- spin structure
+// Chiral basis: gamma_mu = [[0, A_mu], [A_mu^dag, 0]] with
+//   A_x = -i sigma_1, A_y = -i sigma_2, A_z = -i sigma_3, A_t = 1.
+// (1 -+ gamma_mu) psi = (h, -+ A^dag h) with h = psi_up -+ A psi_lo  (A unitary).
+
+template <int MU, typename R>
+__device__ __forceinline__ void mulA(Cx<R> l0, Cx<R> l1, Cx<R>& a0, Cx<R>& a1) {
+  if (MU == 0) { a0 = cmulmi(l1); a1 = cmulmi(l0); }
+  else if (MU == 1) { a0 = cneg(l1); a1 = l0; }
+  else if (MU == 2) { a0 = cmulmi(l0); a1 = cmuli(l1); }
+  else { a0 = l0; a1 = l1; }
+}
+template <int MU, typename R>
+__device__ __forceinline__ void mulAdag(Cx<R> h0, Cx<R> h1, Cx<R>& a0, Cx<R>& a1) {
+  if (MU == 0) { a0 = cmuli(h1); a1 = cmuli(h0); }
+  else if (MU == 1) { a0 = h1; a1 = cneg(h0); }
+  else if (MU == 2) { a0 = cmuli(h0); a1 = cmulmi(h1); }
+  else { a0 = h0; a1 = h1; }
+}
+
+// One direction of the hopping term, both hops, accumulated into acc[12]
+// (acc -= 1/2 [(1 - g) U psi(x+mu) + (1 + g) U(x-mu)^dag psi(x-mu)]).
+// in: spinor planes, element (k, site) at in[k * V + site]; U: link planes.
+template <int MU, typename R>
+__device__ __forceinline__ void hop_dir(const typename Store<R>::T* __restrict__ in,
+                                        const typename Store<R>::T* __restrict__ U, const Geom& g,
+                                        int s, const int c[4], Cx<R> acc[12]) {
+  const int V = g.V;
+#pragma unroll
+  for (int dir = 0; dir < 2; ++dir) {
+    int sgn;
+    const int sn = dir == 0 ? nb_fwd(g, s, c, MU, &sgn) : nb_bwd(g, s, c, MU, &sgn);
+    const int sl = dir == 0 ? s : sn;  // link site
+    // half spinor h[spin 2][colour 3]
+    Cx<R> h0[3], h1[3];
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+      Cx<R> p0 = ld<R>(in + (0 * 3 + col) * (size_t)V + sn);
+      Cx<R> p1 = ld<R>(in + (1 * 3 + col) * (size_t)V + sn);
+      Cx<R> p2 = ld<R>(in + (2 * 3 + col) * (size_t)V + sn);
+      Cx<R> p3 = ld<R>(in + (3 * 3 + col) * (size_t)V + sn);
+      Cx<R> a0, a1;
+      mulA<MU>(p2, p3, a0, a1);
+      if (dir == 0) { h0[col] = csub(p0, a0); h1[col] = csub(p1, a1); }
+      else { h0[col] = cadd(p0, a0); h1[col] = cadd(p1, a1); }
+    }
+    const R f = R(-0.5) * R(sgn);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Cx<R> u0 = {R(0), R(0)}, u1 = {R(0), R(0)};
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        // forward: U[i][j]; backward: (U^dag)[i][j] = conj(U[j][i])
+        const int e = dir == 0 ? (i * 3 + j) : (j * 3 + i);
+        Cx<R> l = ld<R>(U + (MU * 9 + e) * (size_t)V + sl);
+        if (dir == 0) { u0 = cfma(l, h0[j], u0); u1 = cfma(l, h1[j], u1); }
+        else { u0 = cfmaconj(l, h0[j], u0); u1 = cfmaconj(l, h1[j], u1); }
+      }
+      Cx<R> b0, b1;
+      mulAdag<MU>(u0, u1, b0, b1);
+      // upper: += f * u ; lower: += f * (-+ A^dag u)
+      acc[0 * 3 + i] = cadd(acc[0 * 3 + i], cscale(f, u0));
+      acc[1 * 3 + i] = cadd(acc[1 * 3 + i], cscale(f, u1));
+      if (dir == 0) {
+        acc[2 * 3 + i] = csub(acc[2 * 3 + i], cscale(f, b0));
+        acc[3 * 3 + i] = csub(acc[3 * 3 + i], cscale(f, b1));
+      } else {
+        acc[2 * 3 + i] = cadd(acc[2 * 3 + i], cscale(f, b0));
+        acc[3 * 3 + i] = cadd(acc[3 * 3 + i], cscale(f, b1));
+      }
+    }
+  }
+}
+
+// out[12] = (H_W in)(s) = gamma5 [ (4 + m) in(s) - 1/2 sum_mu hops ], r = 1.
+template <typename R>
+__device__ __forceinline__ void hw_site(const typename Store<R>::T* __restrict__ in,
+                                        const typename Store<R>::T* __restrict__ U, const Geom& g,
+                                        int s, R diag, Cx<R> out[12]) {
+  int c[4];
+  site_coords(g, s, c);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) out[k] = cscale(diag, ld<R>(in + k * (size_t)g.V + s));
+  hop_dir<0, R>(in, U, g, s, c, out);
+  hop_dir<1, R>(in, U, g, s, c, out);
+  hop_dir<2, R>(in, U, g, s, c, out);
+  hop_dir<3, R>(in, U, g, s, c, out);
+#pragma unroll
+  for (int k = 6; k < 12; ++k) out[k] = cneg(out[k]);
+}
+
+// ------------------------------------------------------------ reductions
+
+// Deterministic block sum of one double (fixed shuffle tree, fixed warp order).
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh /* >= NT/32 */) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) t += sh[i];
+  }
+  __syncthreads();
+  return t;  // valid in thread 0
+}
+
+// Sum n partials (written by other blocks of this grid) in a fixed order, all threads of the block.
+template <int NT>
+__device__ __forceinline__ double sum_partials(const double* p, int n, double* sh) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += NT) v += __ldcg(p + i);
+  return block_sum<NT>(v, sh);
+}

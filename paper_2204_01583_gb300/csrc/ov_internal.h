@@ -1,0 +1,163 @@
+// Internal declarations of the overlap library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "ov.h"
+
+// ---------------------------------------------------------------- geometry
+
+struct Geom {
+  int L[4];    // Lx, Ly, Lz, Lt
+  int st[4];   // site strides: 1, Lx, Lx*Ly, Lx*Ly*Lz
+  int V;       // sites
+  int bc_t;    // +1 / -1
+};
+
+// ---------------------------------------------------------------- workspace
+
+// A device buffer that grows on demand and is reused across calls.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// Per-kernel-class event timing (ov_set_kernel_timing).
+struct KernelClock {
+  long long launches = 0;
+  double total_ms = 0.0;
+};
+
+struct PendingEvent {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+enum KernelClass {
+  KC_DSLASH = 0,     // H_W apply (plain)
+  KC_LANCZOS_HW,     // dslash + Lanczos epilogue inside the solves
+  KC_SHIFT_UPDATE,   // Lanczos vector update + per-node direction updates + weighted sum
+  KC_LAYOUT,         // pack / unpack / epilogues
+  KC_MISC,           // initialisation and small kernels
+  KC_FORCE,          // link force
+  KC_RESIDUAL,       // FP64 true residuals (mixed mode)
+  KC_COUNT
+};
+
+extern const char* const kKernelClassNames[KC_COUNT];
+
+// Graph cache entry for the per-iteration kernels of a solve: every pointer the
+// captured launches read, plus the launch shape.
+struct GraphKey {
+  const void* ptr[4];
+  int nsrc, nshift, flavour, chunk;
+  bool operator<(const GraphKey& o) const {
+    for (int k = 0; k < 4; ++k)
+      if (ptr[k] != o.ptr[k]) return ptr[k] < o.ptr[k];
+    if (nsrc != o.nsrc) return nsrc < o.nsrc;
+    if (nshift != o.nshift) return nshift < o.nshift;
+    if (flavour != o.flavour) return flavour < o.flavour;
+    return chunk < o.chunk;
+  }
+};
+
+struct ov_ctx {
+  int device = 0;
+  Geom g{};
+  double m0 = 0.0, r = 1.0;
+
+  // gauge field, structure of arrays: element (mu, i, j, site) at [(mu*9 + 3i + j) * V + site]
+  double2* U64 = nullptr;
+  float2* U32 = nullptr;
+  bool have_gauge = false;
+
+  // quadrature S_N = c0 + sum_j c_j (z_j - H)^-1
+  std::vector<double2> z, c;
+  double2 c0{0.0, 0.0};
+  bool have_contour = false;
+
+  // named device workspace
+  std::map<std::string, DevBuf> bufs;
+  int* host_flag = nullptr;  // pinned host word for convergence reads
+  cudaStream_t cap_stream = nullptr;
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+
+  // kernel timing
+  bool timing = false;
+  KernelClock clocks[KC_COUNT];
+  std::vector<PendingEvent> pending;
+  std::vector<cudaEvent_t> event_pool;
+
+  std::string err = "no error";
+};
+
+// ------------------------------------------------------------------ helpers
+
+int ctx_fail(ov_ctx* ctx, int code, const std::string& msg);
+int ctx_cuda(ov_ctx* ctx, cudaError_t e, const char* what);
+void* ws_get(ov_ctx* ctx, const char* name, size_t bytes, int* status);
+void ws_release_all(ov_ctx* ctx);
+void graphs_release(ov_ctx* ctx);
+
+// Kernel timing: bracket a launch with events when ctx->timing is set.
+void kt_begin(ov_ctx* ctx, int cls, cudaStream_t s, cudaEvent_t* a);
+void kt_end(ov_ctx* ctx, int cls, cudaStream_t s, cudaEvent_t a);
+void kt_collect(ov_ctx* ctx);
+
+#define OV_CHECK_LAUNCH(ctx, what)                                  \
+  do {                                                              \
+    cudaError_t e_ = cudaGetLastError();                            \
+    if (e_ != cudaSuccess) return ctx_cuda((ctx), e_, (what));      \
+  } while (0)
+
+// ----------------------------------------------------------- launchers
+
+// layout conversions (dslash.cu)
+int launch_gauge_ingest(ov_ctx* ctx, const double2* U_aos, cudaStream_t s);
+int launch_pack64(ov_ctx* ctx, const double2* aos, double2* soa, int nrhs, cudaStream_t s);
+int launch_unpack64(ov_ctx* ctx, const double2* soa, double2* aos, int nrhs, cudaStream_t s);
+int launch_pack32(ov_ctx* ctx, const float2* aos, float2* soa, int nrhs, cudaStream_t s);
+int launch_unpack32(ov_ctx* ctx, const float2* soa, float2* aos, int nrhs, cudaStream_t s);
+// out (SoA) = H_W in (SoA)
+int launch_hw64(ov_ctx* ctx, const double2* in, double2* out, int nrhs, cudaStream_t s);
+int launch_hw32(ov_ctx* ctx, const float2* in, float2* out, int nrhs, cudaStream_t s);
+// out(AoS) = (1+m)/2 b(AoS) + (1-m)/2 gamma5 s(SoA)
+int launch_overlap_epilogue(ov_ctx* ctx, const double2* b_aos, const double2* s_soa, double2* out_aos,
+                            double m_q, int nrhs, cudaStream_t s);
+// gamma5 on an AoS spinor set (in place allowed)
+int launch_gamma5_aos(ov_ctx* ctx, const double2* in, double2* out, int nrhs, cudaStream_t s);
+
+// solves (solver.cu): out_soa = S_N b_soa for nrhs sources, contour from ctx
+struct SolveOut {
+  int iterations = 0;
+  int converged = 0;
+  double max_residual = 0.0;
+  double error_bound = 0.0;
+  int refine_rounds = 0;
+  int inner_iterations = 0;
+};
+int solve_sign_soa(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nrhs,
+                   const ov_solve_opts& o, SolveOut* so, cudaStream_t s,
+                   double2* xs_soa /* optional per-node solutions [src][node][12V] */);
+
+// Lanczos on H (or H^2) for spectral bounds (solver.cu); fills alpha[0..k), beta[0..k)
+int lanczos_tridiag(ov_ctx* ctx, int steps, int squared, std::vector<double>& alpha,
+                    std::vector<double>& beta, cudaStream_t s);
+
+// force (force.cu): F[mu][site][8] += ... from per-node y and xi (SoA)
+int launch_force(ov_ctx* ctx, const double2* y, const double2* xi, int nnode, const double2* coef,
+                 double* F_aos, cudaStream_t s);
+
+// host-side contour math (contour.cpp)
+void ellipse_rule(int n_q, double gamma, double rho, double alpha, int form, std::vector<double2>& z,
+                  std::vector<double2>& c, double2& c0);
+double rational_value(double lam, const std::vector<double2>& z, const std::vector<double2>& c,
+                      double2 c0);
+void tridiag_extreme_eigs(const std::vector<double>& a, const std::vector<double>& b, double* lo,
+                          double* hi, double* lo_resid, double* hi_resid);

@@ -1,0 +1,654 @@
+// Shifted Krylov solve for every quadrature node at once, and the weighted sum.
+//
+// The paper solves (z_j - H_W) y_j = b for all nodes with a shift solver seeded at
+// z_seed (the shift-solver remark after Eq. 7; shifted BiCG in its numerical
+// section).  For hermitian H_W, BiCG with shadow vector equal to the initial
+// residual produces at step k, for every shift, the Galerkin iterate in the Krylov
+// space K_k(H_W, b): y_{k,j} = V_k (z_j - T_k)^-1 e_1 ||b||, where H_W V_k = V_k T_k +
+// beta_k v_{k+1} e_k^T is the hermitian Lanczos relation with real tridiagonal T_k
+// (alpha_i on the diagonal, beta_i off it).  These iterates do not depend on the seed.
+// We compute exactly them:
+//
+//   * one Lanczos process on H_W per source (kernels K1, K2 below);
+//   * for every node, the LDL^T factorisation of the complex-symmetric tridiagonal
+//     z_j - T_k, updated one row per step:
+//       d_1 = z - alpha_1,  d_i = z - alpha_i - beta_{i-1}^2 / d_{i-1},
+//       l_i = -beta_i / d_i,  omega_1 = ||b||,  omega_i = -l_{i-1} omega_{i-1},
+//       zeta_i = omega_i / d_i;
+//     |Im d_i| >= |Im z| > 0, so no pivot ever vanishes (no breakdown);
+//   * per node the direction p_i = v_i - l_{i-1} p_{i-1} and y += zeta_i p_i, so that
+//     the weighted sum of Eq. 7, s = c0 b + sum_j c_j y_j, is accumulated directly;
+//   * the FOM residual of node j after step i is beta_i |zeta_i| v_{i+1}, so its norm
+//     is known from scalars; a node stops updating once it is below tol ||b||.
+//
+// Lanczos vectors are kept unnormalised, U_i = beta_{i-1} v_i (U_1 = b), in a ring
+// of three buffers; each consumer scales by 1/||U_i||.  All recurrence scalars are
+// FP64 and live on the device; the last block of each kernel (per source) reduces
+// the block partials in a fixed order, so reruns are bit-identical, and updates the
+// scalars.  The host only reads a done counter every few iterations, and replays
+// the per-iteration kernels from a CUDA graph.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int NT1 = 128;  // K1: stencil + Lanczos epilogue
+constexpr int NT2 = 256;  // K2: vector updates
+
+struct SrcState {
+  double bnorm;   // ||b||
+  double n_prev;  // ||U_{i-1}||
+  double n_cur;   // ||U_i||
+  double alpha;   // alpha_i
+  int iter;       // i
+  int done;
+  int status;     // OV_OK, OV_ERR_NOT_CONVERGED, OV_ERR_BREAKDOWN
+  int n_act;
+};
+
+struct ShiftState {
+  double2 d, omega, zeta, l;
+  double res;
+  int active;
+  int last_iter;
+};
+
+struct SolveParams {
+  double tol;
+  int max_iter;
+  int nshift;
+};
+
+// Device pointers of one solve (all in workspace owned by the context).
+template <typename R>
+struct SolveArgs {
+  using T = typename Store<R>::T;
+  T* ring;            // [src][3][12V]
+  T* p;               // [src][nshift][12V]
+  T* x;               // [src][nshift][12V] or null
+  double2* sacc;      // [src][12V] weighted sum (FP64) or null
+  const T* stencil;   // optional pre-applied H U_i for K1 ([src][12V]) or null
+  SrcState* src;
+  ShiftState* sh;     // [src][nshift]
+  const double2* z;   // [src][nshift]
+  const double2* c;   // [src][nshift]
+  int* act_idx;       // [src][nshift]
+  double2* act_l;     // [src][nshift] l_{i-1}
+  double2* act_cz;    // [src][nshift] c_j zeta_i
+  double2* act_z;     // [src][nshift] zeta_i
+  double* part1;      // [src][nblk1]
+  double* part2;      // [src][nblk2]
+  unsigned* cnt;      // [src][2]
+  int* done_count;
+  double* hist_a;     // [src][max_iter] or null
+  double* hist_b;
+  const SolveParams* prm;
+  const T* U;         // links
+  Geom g;
+  R diag;
+};
+
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  const double den = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ void mark_done(SrcState* S, int* done_count, int status) {
+  S->done = 1;
+  S->status = status;
+  atomicAdd(done_count, 1);
+}
+
+// K1: w = H U_i / n_i - (n_i / n_{i-1}) U_{i-1};  alpha_i = Re <U_i, w> / n_i.
+template <typename R>
+__global__ void __launch_bounds__(NT1) lanczos_hw_kernel(SolveArgs<R> a) {
+  using T = typename Store<R>::T;
+  __shared__ double sh[NT1 / 32];
+  __shared__ bool last;
+  const int r = blockIdx.y;
+  SrcState* S = a.src + r;
+  if (S->done) return;
+  const int V = a.g.V;
+  const size_t n12 = (size_t)12 * V;
+  const int i = S->iter;
+  T* base = a.ring + (size_t)r * 3 * n12;
+  const T* Ui = base + (size_t)(i % 3) * n12;
+  const T* Um = base + (size_t)((i + 2) % 3) * n12;
+  T* W = base + (size_t)((i + 1) % 3) * n12;
+  const double inv_n = 1.0 / S->n_cur;
+  const double cm = (i > 1) ? S->n_cur / S->n_prev : 0.0;
+  const int s = blockIdx.x * NT1 + threadIdx.x;
+  double dot = 0.0;
+  if (s < V) {
+    Cx<R> o[12];
+    if (a.stencil) {
+      const T* Hs = a.stencil + (size_t)r * n12;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) o[k] = ld<R>(Hs + k * (size_t)V + s);
+    } else {
+      hw_site<R>(Ui, a.U, a.g, s, a.diag, o);
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const size_t e = k * (size_t)V + s;
+      Cx<R> u = ld<R>(Ui + e);
+      Cx<R> w = cscale((R)inv_n, o[k]);
+      if (i > 1) {
+        Cx<R> um = ld<R>(Um + e);
+        w = csub(w, cscale((R)cm, um));
+      }
+      st<R>(W + e, w);
+      dot += (double)u.re * (double)w.re + (double)u.im * (double)w.im;
+    }
+  }
+  double bs = block_sum<NT1>(dot, sh);
+  if (threadIdx.x == 0) {
+    a.part1[(size_t)r * gridDim.x + blockIdx.x] = bs;
+    __threadfence();
+    last = (atomicAdd(a.cnt + 2 * r, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double tot = sum_partials<NT1>(a.part1 + (size_t)r * gridDim.x, gridDim.x, sh);
+  if (threadIdx.x != 0) return;
+  a.cnt[2 * r] = 0;
+  const double alpha = tot * inv_n;
+  S->alpha = alpha;
+  if (a.hist_a) a.hist_a[(size_t)r * a.prm->max_iter + (i - 1)] = alpha;
+  if (!isfinite(alpha)) {
+    S->n_act = 0;
+    mark_done(S, a.done_count, OV_ERR_BREAKDOWN);
+    return;
+  }
+  // per-node LDL^T row i and the active list for K2
+  const int ns = a.prm->nshift;
+  const double beta_prev = S->n_cur;  // beta_{i-1} = ||U_i|| (i >= 2)
+  int na = 0;
+  for (int j = 0; j < ns; ++j) {
+    ShiftState& q = a.sh[(size_t)r * ns + j];
+    if (!q.active) continue;
+    const double2 zj = a.z[(size_t)r * ns + j];
+    double2 d, om;
+    double2 lprev = make_double2(0.0, 0.0);
+    if (i == 1) {
+      d = make_double2(zj.x - alpha, zj.y);
+      om = make_double2(S->bnorm, 0.0);
+    } else {
+      const double2 t = cdiv(make_double2(beta_prev * beta_prev, 0.0), q.d);
+      d = make_double2(zj.x - alpha - t.x, zj.y - t.y);
+      lprev = q.l;
+      om = cmul(make_double2(-lprev.x, -lprev.y), q.omega);
+    }
+    const double2 zeta = cdiv(om, d);
+    q.d = d;
+    q.omega = om;
+    q.zeta = zeta;
+    const size_t o = (size_t)r * ns + na;
+    a.act_idx[o] = j;
+    a.act_l[o] = lprev;
+    a.act_cz[o] = cmul(a.c[(size_t)r * ns + j], zeta);
+    a.act_z[o] = zeta;
+    ++na;
+  }
+  S->n_act = na;
+}
+
+// K2: U_{i+1} = w - alpha_i U_i / n_i (in place over w), beta_i = ||U_{i+1}||,
+// per active node p = v_i - l_{i-1} p, x += zeta_i p, s += c_j zeta_i p.
+template <typename R>
+__global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
+  using T = typename Store<R>::T;
+  __shared__ double sh[NT2 / 32];
+  __shared__ bool last;
+  const int r = blockIdx.y;
+  SrcState* S = a.src + r;
+  if (S->done) return;
+  const int V = a.g.V;
+  const size_t n12 = (size_t)12 * V;
+  const int i = S->iter;
+  const int ns = a.prm->nshift;
+  T* base = a.ring + (size_t)r * 3 * n12;
+  const T* Ui = base + (size_t)(i % 3) * n12;
+  T* W = base + (size_t)((i + 1) % 3) * n12;
+  const double inv_n = 1.0 / S->n_cur;
+  const double alpha = S->alpha;
+  const int na = S->n_act;
+  const size_t e = (size_t)blockIdx.x * NT2 + threadIdx.x;
+  double nrm = 0.0;
+  if (e < n12) {
+    Cx<R> v = cscale((R)inv_n, ld<R>(Ui + e));
+    Cx<R> w = ld<R>(W + e);
+    Cx<R> u = csub(w, cscale((R)alpha, v));
+    st<R>(W + e, u);
+    nrm = (double)u.re * (double)u.re + (double)u.im * (double)u.im;
+    double sre = 0.0, sim = 0.0;
+    const int* idx = a.act_idx + (size_t)r * ns;
+    const double2* al = a.act_l + (size_t)r * ns;
+    const double2* acz = a.act_cz + (size_t)r * ns;
+    const double2* az = a.act_z + (size_t)r * ns;
+    for (int k = 0; k < na; ++k) {
+      const int j = __ldg(idx + k);
+      T* P = a.p + ((size_t)r * ns + j) * n12 + e;
+      Cx<R> pv = v;
+      if (i > 1) {
+        const double2 l = __ldg(al + k);
+        Cx<R> po = ld<R>(P);
+        pv.re = v.re - ((R)l.x * po.re - (R)l.y * po.im);
+        pv.im = v.im - ((R)l.x * po.im + (R)l.y * po.re);
+      }
+      st<R>(P, pv);
+      const double2 cz = __ldg(acz + k);
+      sre += cz.x * (double)pv.re - cz.y * (double)pv.im;
+      sim += cz.x * (double)pv.im + cz.y * (double)pv.re;
+      if (a.x) {
+        const double2 zt = __ldg(az + k);
+        T* X = a.x + ((size_t)r * ns + j) * n12 + e;
+        Cx<R> xo = (i > 1) ? ld<R>(X) : Cx<R>{R(0), R(0)};
+        xo.re += (R)zt.x * pv.re - (R)zt.y * pv.im;
+        xo.im += (R)zt.x * pv.im + (R)zt.y * pv.re;
+        st<R>(X, xo);
+      }
+    }
+    if (a.sacc && na > 0) {
+      double2* Sx = a.sacc + (size_t)r * n12 + e;
+      double2 sv = *Sx;
+      sv.x += sre;
+      sv.y += sim;
+      *Sx = sv;
+    }
+  }
+  double bs = block_sum<NT2>(nrm, sh);
+  if (threadIdx.x == 0) {
+    a.part2[(size_t)r * gridDim.x + blockIdx.x] = bs;
+    __threadfence();
+    last = (atomicAdd(a.cnt + 2 * r + 1, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double tot = sum_partials<NT2>(a.part2 + (size_t)r * gridDim.x, gridDim.x, sh);
+  if (threadIdx.x != 0) return;
+  a.cnt[2 * r + 1] = 0;
+  const double beta = sqrt(tot);
+  if (a.hist_b) a.hist_b[(size_t)r * a.prm->max_iter + (i - 1)] = beta;
+  if (!isfinite(beta)) {
+    mark_done(S, a.done_count, OV_ERR_BREAKDOWN);
+    return;
+  }
+  const double tol = a.prm->tol;
+  int still = 0;
+  for (int j = 0; j < ns; ++j) {
+    ShiftState& q = a.sh[(size_t)r * ns + j];
+    if (!q.active) continue;
+    q.res = beta * sqrt(q.zeta.x * q.zeta.x + q.zeta.y * q.zeta.y) / S->bnorm;
+    q.l = cdiv(make_double2(-beta, 0.0), q.d);
+    q.last_iter = i;
+    if (q.res <= tol || beta == 0.0) {
+      q.active = 0;
+      if (beta == 0.0) q.res = 0.0;
+    } else {
+      ++still;
+    }
+  }
+  S->n_prev = S->n_cur;
+  S->n_cur = beta;
+  S->iter = i + 1;
+  if (beta == 0.0) {
+    mark_done(S, a.done_count, OV_OK);
+  } else if (ns > 0 && still == 0) {
+    mark_done(S, a.done_count, OV_OK);
+  } else if (i >= a.prm->max_iter) {
+    mark_done(S, a.done_count, ns > 0 ? OV_ERR_NOT_CONVERGED : OV_OK);
+  }
+}
+
+// Init: U_1 = b (ring slot 1), ||b|| per source, s = c0 b, node states reset.
+template <typename R>
+__global__ void __launch_bounds__(NT2) lanczos_init_kernel(SolveArgs<R> a, const double2* __restrict__ b,
+                                                           double2 c0) {
+  using T = typename Store<R>::T;
+  __shared__ double sh[NT2 / 32];
+  __shared__ bool last;
+  const int r = blockIdx.y;
+  const size_t n12 = (size_t)12 * a.g.V;
+  T* U1 = a.ring + (size_t)r * 3 * n12 + n12;
+  const size_t e = (size_t)blockIdx.x * NT2 + threadIdx.x;
+  double nrm = 0.0;
+  if (e < n12) {
+    const double2 bv = b[(size_t)r * n12 + e];
+    T t;
+    t.x = bv.x;
+    t.y = bv.y;
+    U1[e] = t;
+    nrm = bv.x * bv.x + bv.y * bv.y;
+    if (a.sacc) a.sacc[(size_t)r * n12 + e] = make_double2(c0.x * bv.x - c0.y * bv.y, c0.x * bv.y + c0.y * bv.x);
+  }
+  double bs = block_sum<NT2>(nrm, sh);
+  if (threadIdx.x == 0) {
+    a.part2[(size_t)r * gridDim.x + blockIdx.x] = bs;
+    __threadfence();
+    last = (atomicAdd(a.cnt + 2 * r + 1, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double tot = sum_partials<NT2>(a.part2 + (size_t)r * gridDim.x, gridDim.x, sh);
+  if (threadIdx.x != 0) return;
+  a.cnt[2 * r + 1] = 0;
+  SrcState* S = a.src + r;
+  S->bnorm = sqrt(tot);
+  S->n_cur = S->bnorm;
+  S->n_prev = 1.0;
+  S->alpha = 0.0;
+  S->iter = 1;
+  S->status = OV_OK;
+  S->n_act = 0;
+  S->done = 0;
+  const int ns = a.prm->nshift;
+  for (int j = 0; j < ns; ++j) {
+    ShiftState& q = a.sh[(size_t)r * ns + j];
+    q.d = q.omega = q.zeta = q.l = make_double2(0.0, 0.0);
+    q.res = 1.0;
+    q.active = 1;
+    q.last_iter = 0;
+  }
+  if (!(S->bnorm > 0.0) || !isfinite(S->bnorm)) {
+    for (int j = 0; j < ns; ++j) {
+      a.sh[(size_t)r * ns + j].active = 0;
+      a.sh[(size_t)r * ns + j].res = 0.0;
+    }
+    mark_done(S, a.done_count, isfinite(S->bnorm) ? OV_OK : OV_ERR_BREAKDOWN);
+  }
+}
+
+// zero the per-node solution buffers (first update writes them, but a node that is
+// converged at init must still read as zero)
+template <typename T>
+__global__ void zero_kernel(T* p, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    T z;
+    z.x = 0;
+    z.y = 0;
+    p[t] = z;
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+
+namespace {
+
+template <typename R>
+struct SolveWs {
+  SolveArgs<R> a{};
+  int nblk1 = 0, nblk2 = 0;
+  SolveParams* prm_dev = nullptr;
+};
+
+template <typename R>
+int setup_ws(ov_ctx* ctx, int nsrc, int ns, bool want_x, bool want_sacc, bool want_hist, int max_iter,
+             SolveWs<R>* w, const char* tag) {
+  using T = typename Store<R>::T;
+  const int V = ctx->g.V;
+  const size_t n12 = (size_t)12 * V;
+  int st = OV_OK;
+  std::string t(tag);
+  w->nblk1 = (V + NT1 - 1) / NT1;
+  w->nblk2 = (int)((n12 + NT2 - 1) / NT2);
+  auto& a = w->a;
+  a.ring = (T*)ws_get(ctx, (t + ".ring").c_str(), sizeof(T) * 3 * n12 * nsrc, &st);
+  a.p = ns ? (T*)ws_get(ctx, (t + ".p").c_str(), sizeof(T) * n12 * (size_t)nsrc * ns, &st) : nullptr;
+  a.x = (want_x && ns) ? (T*)ws_get(ctx, (t + ".x").c_str(), sizeof(T) * n12 * (size_t)nsrc * ns, &st) : nullptr;
+  a.sacc = want_sacc ? (double2*)ws_get(ctx, (t + ".sacc").c_str(), sizeof(double2) * n12 * nsrc, &st) : nullptr;
+  a.src = (SrcState*)ws_get(ctx, (t + ".src").c_str(), sizeof(SrcState) * nsrc, &st);
+  const size_t nsh = (size_t)nsrc * (ns > 0 ? ns : 1);
+  a.sh = (ShiftState*)ws_get(ctx, (t + ".sh").c_str(), sizeof(ShiftState) * nsh, &st);
+  a.z = (const double2*)ws_get(ctx, (t + ".z").c_str(), sizeof(double2) * nsh, &st);
+  a.c = (const double2*)ws_get(ctx, (t + ".c").c_str(), sizeof(double2) * nsh, &st);
+  a.act_idx = (int*)ws_get(ctx, (t + ".aidx").c_str(), sizeof(int) * nsh, &st);
+  a.act_l = (double2*)ws_get(ctx, (t + ".al").c_str(), sizeof(double2) * nsh, &st);
+  a.act_cz = (double2*)ws_get(ctx, (t + ".acz").c_str(), sizeof(double2) * nsh, &st);
+  a.act_z = (double2*)ws_get(ctx, (t + ".az").c_str(), sizeof(double2) * nsh, &st);
+  a.part1 = (double*)ws_get(ctx, (t + ".part1").c_str(), sizeof(double) * (size_t)w->nblk1 * nsrc, &st);
+  a.part2 = (double*)ws_get(ctx, (t + ".part2").c_str(), sizeof(double) * (size_t)w->nblk2 * nsrc, &st);
+  a.cnt = (unsigned*)ws_get(ctx, (t + ".cnt").c_str(), sizeof(unsigned) * 2 * nsrc, &st);
+  a.done_count = (int*)ws_get(ctx, (t + ".done").c_str(), sizeof(int), &st);
+  if (want_hist) {
+    a.hist_a = (double*)ws_get(ctx, (t + ".ha").c_str(), sizeof(double) * (size_t)nsrc * max_iter, &st);
+    a.hist_b = (double*)ws_get(ctx, (t + ".hb").c_str(), sizeof(double) * (size_t)nsrc * max_iter, &st);
+  } else {
+    a.hist_a = a.hist_b = nullptr;
+  }
+  w->prm_dev = (SolveParams*)ws_get(ctx, (t + ".prm").c_str(), sizeof(SolveParams), &st);
+  a.prm = w->prm_dev;
+  a.stencil = nullptr;
+  a.g = ctx->g;
+  a.diag = (R)(4.0 - ctx->m0);
+  if (sizeof(R) == 8)
+    a.U = (const T*)ctx->U64;
+  else
+    a.U = (const T*)ctx->U32;
+  return st;
+}
+
+template <typename R>
+int launch_iteration(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, cudaStream_t s) {
+  cudaEvent_t ev;
+  kt_begin(ctx, KC_LANCZOS_HW, s, &ev);
+  lanczos_hw_kernel<R><<<dim3(w.nblk1, nsrc), NT1, 0, s>>>(w.a);
+  kt_end(ctx, KC_LANCZOS_HW, s, ev);
+  kt_begin(ctx, KC_SHIFT_UPDATE, s, &ev);
+  lanczos_update_kernel<R><<<dim3(w.nblk2, nsrc), NT2, 0, s>>>(w.a);
+  kt_end(ctx, KC_SHIFT_UPDATE, s, ev);
+  return OV_OK;
+}
+
+// Run iterations until every source is done or max_iter is reached.
+template <typename R>
+int run_iterations(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, int nshift, int flavour, int max_iter,
+                   const ov_solve_opts& o, cudaStream_t s) {
+  const int chunk = o.check_every > 0 ? o.check_every : 32;
+  const bool graph = o.use_graph && !ctx->timing;
+  cudaGraphExec_t exec = nullptr;
+  if (graph) {
+    GraphKey key{{(const void*)w.a.ring, (const void*)w.a.p, (const void*)w.a.x, (const void*)w.a.sacc},
+                 nsrc, nshift, flavour, chunk};
+    auto it = ctx->graphs.find(key);
+    if (it != ctx->graphs.end()) {
+      exec = it->second;
+    } else {
+      // the graph replays identical launches: every argument is a workspace pointer
+      // and all per-iteration state lives in device memory
+      cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaStreamBeginCapture");
+      for (int k = 0; k < chunk; ++k) {
+        lanczos_hw_kernel<R><<<dim3(w.nblk1, nsrc), NT1, 0, ctx->cap_stream>>>(w.a);
+        lanczos_update_kernel<R><<<dim3(w.nblk2, nsrc), NT2, 0, ctx->cap_stream>>>(w.a);
+      }
+      cudaGraph_t gph = nullptr;
+      e = cudaStreamEndCapture(ctx->cap_stream, &gph);
+      if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&exec, gph, 0);
+      cudaGraphDestroy(gph);
+      if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaGraphInstantiate");
+      ctx->graphs[key] = exec;
+    }
+  }
+  int done_iters = 0;
+  while (done_iters < max_iter) {
+    const int n = std::min(chunk, max_iter - done_iters);
+    if (graph && n == chunk) {
+      cudaError_t e = cudaGraphLaunch(exec, s);
+      if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaGraphLaunch");
+    } else {
+      for (int k = 0; k < n; ++k) launch_iteration<R>(ctx, w, nsrc, s);
+      OV_CHECK_LAUNCH(ctx, "lanczos kernels");
+    }
+    done_iters += n;
+    cudaError_t e = cudaMemcpyAsync(ctx->host_flag, w.a.done_count, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaMemcpyAsync(done)");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaStreamSynchronize");
+    kt_collect(ctx);
+    if (*ctx->host_flag >= nsrc) break;
+  }
+  return OV_OK;
+}
+
+template <typename R>
+int init_solve(ov_ctx* ctx, SolveWs<R>& w, const double2* b_soa, int nsrc, int ns,
+               const std::vector<double2>& zh, const std::vector<double2>& ch, double2 c0,
+               double tol, int max_iter, cudaStream_t s) {
+  SolveParams prm{tol, max_iter, ns};
+  cudaError_t e = cudaMemcpyAsync(w.prm_dev, &prm, sizeof(prm), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy params");
+  if (ns > 0) {
+    e = cudaMemcpyAsync((void*)w.a.z, zh.data(), sizeof(double2) * zh.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy nodes");
+    e = cudaMemcpyAsync((void*)w.a.c, ch.data(), sizeof(double2) * ch.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy coefficients");
+  }
+  cudaMemsetAsync(w.a.cnt, 0, sizeof(unsigned) * 2 * nsrc, s);
+  cudaMemsetAsync(w.a.done_count, 0, sizeof(int), s);
+  if (w.a.x) {
+    const size_t n = (size_t)12 * ctx->g.V * nsrc * ns;
+    zero_kernel<typename Store<R>::T><<<1024, 256, 0, s>>>(w.a.x, n);
+  }
+  cudaEvent_t ev;
+  kt_begin(ctx, KC_MISC, s, &ev);
+  lanczos_init_kernel<R><<<dim3(w.nblk2, nsrc), NT2, 0, s>>>(w.a, b_soa, c0);
+  kt_end(ctx, KC_MISC, s, ev);
+  OV_CHECK_LAUNCH(ctx, "lanczos_init_kernel");
+  return OV_OK;
+}
+
+template <typename R>
+int finish_solve(ov_ctx* ctx, SolveWs<R>& w, int nsrc, int ns, const std::vector<double2>& zh,
+                 const std::vector<double2>& ch, SolveOut* so, cudaStream_t s) {
+  std::vector<SrcState> S(nsrc);
+  std::vector<ShiftState> Q((size_t)nsrc * (ns > 0 ? ns : 1));
+  cudaError_t e = cudaMemcpyAsync(S.data(), w.a.src, sizeof(SrcState) * nsrc, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && ns > 0)
+    e = cudaMemcpyAsync(Q.data(), w.a.sh, sizeof(ShiftState) * (size_t)nsrc * ns, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "read solver state");
+  int status = OV_OK;
+  so->iterations = 0;
+  so->converged = 1;
+  so->max_residual = 0.0;
+  so->error_bound = 0.0;
+  for (int r = 0; r < nsrc; ++r) {
+    so->iterations = std::max(so->iterations, S[r].iter - 1);
+    if (!S[r].done) S[r].status = OV_ERR_NOT_CONVERGED;
+    if (S[r].status != OV_OK) {
+      so->converged = 0;
+      if (status == OV_OK || S[r].status == OV_ERR_BREAKDOWN) status = S[r].status;
+    }
+    double bound = 0.0;
+    for (int j = 0; j < ns; ++j) {
+      const ShiftState& q = Q[(size_t)r * ns + j];
+      so->max_residual = std::max(so->max_residual, q.res);
+      const double2 zz = zh[(size_t)r * ns + j], cc = ch[(size_t)r * ns + j];
+      bound += std::hypot(cc.x, cc.y) * q.res / std::fabs(zz.y);
+    }
+    so->error_bound = std::max(so->error_bound, bound);
+  }
+  if (status == OV_ERR_NOT_CONVERGED)
+    return ctx_fail(ctx, status, "shifted solve hit the iteration limit before every node met tol");
+  if (status == OV_ERR_BREAKDOWN) return ctx_fail(ctx, status, "non-finite Lanczos scalar (NaN/Inf in input?)");
+  return OV_OK;
+}
+
+}  // namespace
+
+int solve_sign_soa(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc, const ov_solve_opts& o,
+                   SolveOut* so, cudaStream_t s, double2* xs_soa) {
+  const int ns = (int)ctx->z.size();
+  SolveWs<double> w;
+  int st = setup_ws<double>(ctx, nsrc, ns, xs_soa != nullptr, true, false, o.max_iter, &w, "fp64");
+  if (st != OV_OK) return st;
+  if (xs_soa) w.a.x = xs_soa;
+  std::vector<double2> zh((size_t)nsrc * ns), ch((size_t)nsrc * ns);
+  for (int r = 0; r < nsrc; ++r)
+    for (int j = 0; j < ns; ++j) {
+      zh[(size_t)r * ns + j] = ctx->z[j];
+      ch[(size_t)r * ns + j] = ctx->c[j];
+    }
+  st = init_solve<double>(ctx, w, b_soa, nsrc, ns, zh, ch, ctx->c0, o.tol, o.max_iter, s);
+  if (st != OV_OK) return st;
+  st = run_iterations<double>(ctx, w, nsrc, ns, xs_soa ? 1 : 0, o.max_iter, o, s);
+  if (st != OV_OK) return st;
+  st = finish_solve<double>(ctx, w, nsrc, ns, zh, ch, so, s);
+  // copy the weighted sum out even when not converged (best iterate)
+  cudaError_t e = cudaMemcpyAsync(out_soa, w.a.sacc, sizeof(double2) * 12 * (size_t)ctx->g.V * nsrc,
+                                  cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy sum");
+  return st;
+}
+
+// Lanczos tridiagonal of H_W (squared = 0) or H_W^2 (squared = 1) from a fixed
+// pseudo-random start vector; returns alpha[0..k), beta[0..k).
+namespace {
+__global__ void start_vector_kernel(double2* v, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    // splitmix64 of the element index: a fixed, reproducible start vector
+    unsigned long long x = t + 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    const double a = (double)(x & 0xFFFFFFFFull) / 4294967296.0 - 0.5;
+    const double b = (double)(x >> 32) / 4294967296.0 - 0.5;
+    v[t] = make_double2(a, b);
+  }
+}
+}  // namespace
+
+int lanczos_tridiag(ov_ctx* ctx, int steps, int squared, std::vector<double>& alpha, std::vector<double>& beta,
+                    cudaStream_t s) {
+  SolveWs<double> w;
+  int st = setup_ws<double>(ctx, 1, 0, false, false, true, steps, &w, "lz");
+  if (st != OV_OK) return st;
+  const size_t n12 = (size_t)12 * ctx->g.V;
+  double2* b = (double2*)ws_get(ctx, "lz.b", sizeof(double2) * n12, &st);
+  double2* tmp = squared ? (double2*)ws_get(ctx, "lz.tmp", sizeof(double2) * n12, &st) : nullptr;
+  double2* tmp2 = squared ? (double2*)ws_get(ctx, "lz.tmp2", sizeof(double2) * n12, &st) : nullptr;
+  if (st != OV_OK) return st;
+  start_vector_kernel<<<256, 256, 0, s>>>(b, n12);
+  std::vector<double2> none;
+  st = init_solve<double>(ctx, w, b, 1, 0, none, none, make_double2(0, 0), 0.0, steps, s);
+  if (st != OV_OK) return st;
+  for (int it = 0; it < steps; ++it) {
+    SolveArgs<double> a = w.a;
+    if (squared) {
+      // H^2: apply H twice to U_i (ring slot i % 3, i = it + 1); K1 reads the result
+      const double2* Ui = w.a.ring + (size_t)((it + 1) % 3) * n12;
+      st = launch_hw64(ctx, Ui, tmp, 1, s);
+      if (st == OV_OK) st = launch_hw64(ctx, tmp, tmp2, 1, s);
+      if (st != OV_OK) return st;
+      a.stencil = tmp2;
+    }
+    lanczos_hw_kernel<double><<<dim3(w.nblk1, 1), NT1, 0, s>>>(a);
+    lanczos_update_kernel<double><<<dim3(w.nblk2, 1), NT2, 0, s>>>(a);
+  }
+  OV_CHECK_LAUNCH(ctx, "lanczos bound kernels");
+  SrcState S;
+  cudaError_t e = cudaMemcpyAsync(&S, w.a.src, sizeof(S), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "lanczos state");
+  const int k = S.iter - 1;
+  if (S.status == OV_ERR_BREAKDOWN || k < 1) return ctx_fail(ctx, OV_ERR_BREAKDOWN, "Lanczos bound breakdown");
+  alpha.resize(k);
+  beta.resize(k);
+  e = cudaMemcpy(alpha.data(), w.a.hist_a, sizeof(double) * k, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(beta.data(), w.a.hist_b, sizeof(double) * k, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "lanczos history");
+  return OV_OK;
+}

@@ -1,0 +1,183 @@
+"""sgn(H_W) b and D_ov(m_q) b on the GPU against the oracle, through the C ABI (GPU).
+
+Parity: the GPU weighted sum of shifted-solver iterates vs the oracle's per-node
+CGNR (or dense LU) resolvents and sum, same nodes, to 1e-10 relative.  Accuracy:
+the same operator vs the exact spectral sign function (dense zheevd) within the
+method error predicted from the spectrum.
+"""
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import cimpl, contour, freefield, sign, wilson
+from tests.gpu_common import M0, make_ctx, rel, sgn_gpu, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+PARITY = 1e-10
+
+
+def _oracle(U, b, ctx, tol=1e-13):
+    z, c, c0 = ctx.get_contour()
+    out, iters, res = cimpl.sign_apply(U, b, z, c, c0, M0, tol=tol)
+    return out
+
+
+def test_config1_4x4_dense(gpu_lib):
+    """4^4, eps = 0.3, N_q = 32 from Lanczos placement: parity with the per-node oracle,
+    accuracy vs dense zheevd sgn, GW relation and sgn^2 = 1 within the predicted error."""
+    dims = (4, 4, 4, 4)
+    ctx, U = make_ctx(gpu_lib, dims, 0.3, S.seed_for("config1"))
+    spec = ctx.place_contour(32, steps=120)
+    b = S.gaussian_spinor(dims, S.seed_for("config1.b"))
+    got, st = sgn_gpu(ctx, b, tol=1e-12)
+    assert st["converged"] == 1
+    want = _oracle(U, b, ctx)
+    assert rel(got, want) < PARITY
+    # exact sign function and the method error predicted from the true spectrum
+    H = wilson.dense_HW(U, M0)
+    lam, V = np.linalg.eigh(H)
+    z, c, c0 = ctx.get_contour()
+    rl = contour.rational(lam, z, c, c0).real
+    method_err = np.abs(rl - np.sign(lam)).max()
+    assert abs(spec["lambda_max"] - lam.max()) < 1e-6 * lam.max()
+    assert abs(spec["lambda_min"] - lam.min()) < 1e-6 * abs(lam.min())
+    # the placement's prediction (from Lanczos bounds) matches the error on the true spectrum
+    assert method_err <= 2.0 * spec["predicted_error"] + 1e-12
+    assert spec["predicted_error"] < 1e-2
+    x = b.reshape(-1)
+    exact = (V * np.sign(lam)) @ (V.conj().T @ x)
+    assert np.linalg.norm(got.reshape(-1) - exact) / np.linalg.norm(x) <= 1.01 * method_err + 1e-11
+    # GW: {gamma5, D} - 2 D gamma5 D = gamma5 (1 - S^2)/2 at m_q = 0
+    import torch
+
+    Sb = to_dev(got)
+    S2b = torch.empty_like(Sb)
+    ctx.sgn(Sb, S2b, 1)
+    s2 = to_host(S2b)
+    assert np.linalg.norm(s2 - b) / np.linalg.norm(b) <= 2.01 * method_err + 1e-10
+    assert sign.sigma(b, got) <= 2.01 * method_err + 1e-10
+
+
+def test_config2_8x4_parity(gpu_lib):
+    """8^4, eps = 0.5, N_q = 64, tol 1e-12: 4 sources in one call; one source against the
+    per-node CGNR oracle at 1e-10, all four: sgn^2 b = b within the predicted method error."""
+    import torch
+
+    dims = (8, 8, 8, 8)
+    ctx, U = make_ctx(gpu_lib, dims, 0.5, S.seed_for("config2"))
+    spec = ctx.place_contour(64, steps=150)
+    b = S.gaussian_spinor(dims, S.seed_for("config2.b"), n=4)
+    got, st = sgn_gpu(ctx, b, nrhs=4, tol=1e-12)
+    assert st["converged"] == 1 and st["max_residual"] <= 1e-12
+    want = _oracle(U, b[0], ctx)
+    assert rel(got[0], want) < PARITY
+    # sgn^2 = 1 on all four sources
+    S2 = torch.empty_like(to_dev(got))
+    ctx.sgn(to_dev(got), S2, 4)
+    s2 = to_host(S2)
+    for k in range(4):
+        assert rel(s2[k], b[k]) < max(10 * spec["predicted_error"], 1e-9)
+
+
+def test_ragged_lattice_parity(gpu_lib):
+    """Lattice whose volume is not a multiple of any block size."""
+    dims = (3, 5, 4, 6)
+    ctx, U = make_ctx(gpu_lib, dims, 0.5, 51)
+    ctx.set_contour_ellipse(24, 3.4, 3.4, 0.3)
+    b = S.gaussian_spinor(dims, 52)
+    got, st = sgn_gpu(ctx, b, tol=1e-12)
+    assert rel(got, _oracle(U, b, ctx)) < PARITY
+
+
+def test_free_field_closed_form_8x4(gpu_lib):
+    dims = (8, 8, 8, 8)
+    ctx, _ = make_ctx(gpu_lib, dims, 0.0, 0)
+    ctx.set_contour_ellipse(48, 3.4, 3.4, 0.3)
+    b = S.gaussian_spinor(dims, 61)
+    got, st = sgn_gpu(ctx, b, tol=1e-13)
+    z, c, c0 = ctx.get_contour()
+    want = freefield.apply_function(b, lambda e: contour.rational(e, z, c, c0), M0)
+    assert rel(got, want) < PARITY
+
+
+def test_paper_two_contour_form(gpu_lib):
+    """Eq. 5 form (two ellipses, c0 = 0) with the paper's alpha = 0.1, scaled to enclose the spectrum."""
+    dims = (4, 4, 4, 4)
+    ctx, U = make_ctx(gpu_lib, dims, 0.3, 71)
+    ctx.set_contour_ellipse(48, 3.4, 3.39999, 0.1, gpu_lib.OV_CONTOUR_PAIR)
+    z, c, c0 = ctx.get_contour()
+    zr, cr, c0r = contour.paper_two_contour(48, 3.4, 3.39999, 0.1)
+    assert np.allclose(z, zr, rtol=0, atol=1e-14) and np.allclose(c, cr, rtol=0, atol=1e-15) and c0 == c0r
+    b = S.gaussian_spinor(dims, 72)
+    got, st = sgn_gpu(ctx, b, tol=1e-12)
+    assert rel(got, _oracle(U, b, ctx)) < PARITY
+
+
+def test_overlap_epilogue(gpu_lib):
+    import torch
+
+    dims = (4, 4, 4, 4)
+    ctx, U = make_ctx(gpu_lib, dims, 0.3, 81)
+    ctx.set_contour_ellipse(32, 3.4, 3.4, 0.3)
+    b = S.gaussian_spinor(dims, 82)
+    s, _ = sgn_gpu(ctx, b)
+    out = torch.empty_like(to_dev(b))
+    ctx.overlap(0.1, to_dev(b), out, 1)
+    want = sign.overlap_from_sign(b, _oracle(U, b, ctx), 0.1)
+    assert rel(to_host(out), want) < PARITY
+
+
+def test_host_io_matches_device_io(gpu_lib):
+    dims = (4, 4, 4, 4)
+    ctx, U = make_ctx(gpu_lib, dims, 0.3, 91)
+    ctx.set_contour_ellipse(32, 3.4, 3.4, 0.3)
+    b = S.gaussian_spinor(dims, 92)
+    dev, _ = sgn_gpu(ctx, b)
+    out = np.empty_like(b)
+    ctx.sgn(b, out, 1, ctx.opts(host_io=True))
+    assert np.array_equal(out, dev)
+
+
+def test_graph_and_direct_launch_agree_bitwise(gpu_lib):
+    dims = (4, 4, 4, 4)
+    ctx, U = make_ctx(gpu_lib, dims, 0.3, 93)
+    ctx.set_contour_ellipse(32, 3.4, 3.4, 0.3)
+    b = S.gaussian_spinor(dims, 94, n=2)
+    a1, _ = sgn_gpu(ctx, b, use_graph=True)
+    a2, _ = sgn_gpu(ctx, b, use_graph=False, check_every=7)
+    assert np.array_equal(a1, a2)
+
+
+def test_edge_cases(gpu_lib):
+    import torch
+
+    dims = (4, 4, 4, 4)
+    ctx, U = make_ctx(gpu_lib, dims, 0.3, 95)
+    ctx.set_contour_ellipse(16, 3.4, 3.4, 0.3)
+    # zero source -> zero output
+    z0, st = sgn_gpu(ctx, np.zeros(S.lattice_shape(dims) + (4, 3), np.complex128))
+    assert np.all(z0 == 0) and st["converged"] == 1
+    # iteration cap -> NOT_CONVERGED, output holds the current iterate
+    b = S.gaussian_spinor(dims, 96)
+    bd = to_dev(b)
+    out = torch.empty_like(bd)
+    st = ctx.sgn(bd, out, 1, ctx.opts(max_iter=3), allow_not_converged=True)
+    assert st["status"] == gpu_lib.OV_ERR_NOT_CONVERGED and st["converged"] == 0
+    # NaN in the source -> BREAKDOWN status, no hang
+    bn = b.copy()
+    bn[0, 0, 0, 0, 0, 0] = np.nan
+    with pytest.raises(gpu_lib.OvError) as e:
+        sgn_gpu(ctx, bn)
+    assert e.value.code == gpu_lib.OV_ERR_BREAKDOWN
+    # nrhs = 0 is a no-op
+    ctx.sgn(bd, out, 0)
+    # bad options
+    with pytest.raises(gpu_lib.OvError):
+        ctx.sgn(bd, out, 1, ctx.opts(tol=0.0))
+    # no contour
+    ctx2 = gpu_lib.Context(dims)
+    ctx2.set_gauge(to_dev(U))
+    with pytest.raises(gpu_lib.OvError) as e:
+        ctx2.sgn(bd, out, 1)
+    assert e.value.code == gpu_lib.OV_ERR_NO_CONTOUR
