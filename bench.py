@@ -1,0 +1,434 @@
+#!/usr/bin/env python
+"""Benchmark of the contour-integral overlap path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--mode MODE]
+    python bench.py --impl reference ...
+
+A step is one pass of the hot path over one batch of synthetic sources:
+D_ov(m_q) b = (1+m_q)/2 b + (1-m_q)/2 gamma5 S_N b for every source of the batch,
+S_N b = c0 b + sum_j c_j (z_j - H_W)^-1 b from one shifted Krylov solve (Eqs. 1, 5-7).
+The contour is placed once per gauge field from Lanczos bounds (setup, untimed).
+The metric is source applies per second.  Prints ONE JSON line on rank 0.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on
+the launching stream; a 256 MiB buffer is written between timed steps to flush
+L2; barrier + synchronize on both sides; max over ranks.  The end-to-end figure
+repeats the K steps through the same C-ABI call with pinned HOST buffers (copies
+inside the timed region).  Kernel durations for the roofline come from the
+library's per-launch CUDA events on the same stream (a separate K-step pass,
+because the timed pass replays CUDA graphs that cannot hold those events).
+
+--impl reference times the FP64 CPU oracle (per-node CGNR solves and the
+weighted sum) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "sgn(H_W)·b applies/s and dslash HBM GB/s vs roofline; batched-mixed vs FP64"
+UNIT = "applies/s"
+
+# FP64 arithmetic peak of one GB300 (profiling recipe's nominal table); HBM from MEASURED_PEAKS.json
+FP64_PEAK_TFLOPS = 1.25
+HBM_FALLBACK_GBS = 6800.0
+
+WORKLOADS = {
+    # name: lattice, link roughness, quark mass, nodes, sources, source kind, tolerance, solver mode
+    "8^4-fp64-nq64-4src": dict(dims=(8, 8, 8, 8), eps=0.5, m_q=0.05, n_q=64, nsrc=4, src="gauss", tol=1e-12,
+                               mode="fp64"),
+    "4^4-fp64-nq32-1src": dict(dims=(4, 4, 4, 4), eps=0.3, m_q=0.1, n_q=32, nsrc=1, src="gauss", tol=1e-12,
+                               mode="fp64"),
+    "16^4-nq64-12pt": dict(dims=(16, 16, 16, 16), eps=0.5, m_q=0.05, n_q=64, nsrc=12, src="point", tol=1e-12,
+                           mode="mixed"),
+    "16^3x32-nq64-12pt": dict(dims=(16, 16, 16, 32), eps=0.6, m_q=0.01, n_q=64, nsrc=12, src="point", tol=1e-12,
+                              mode="mixed"),
+}
+DEFAULT_WORKLOAD = "8^4-fp64-nq64-4src"
+M0 = 1.6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default=None, choices=[None, "fp64", "fp64_2pass", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_inputs(wl, rank):
+    import synthetic as S
+
+    dims = wl["dims"]
+    U = S.su3_links(dims, wl["eps"], S.seed_for("gauge:" + "x".join(map(str, dims))))
+    if wl["src"] == "gauss":
+        b = S.gaussian_spinor(dims, S.seed_for(f"src:{rank}"), n=wl["nsrc"])
+    else:
+        b = S.point_sources(dims)[: wl["nsrc"]]
+    return U, b
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- oracle (CPU)
+
+def oracle_sample(U, b0, z, c, c0, stride):
+    """Time the FP64 CPU oracle on every `stride`-th node of one source; returns
+    (seconds, nodes timed, threads)."""
+    from oracle import cimpl
+
+    cimpl.build()
+    idx = np.arange(0, len(z), stride)
+    t0 = time.perf_counter()
+    cimpl.sign_apply(U, b0, z[idx], c[idx], 0.0, M0, tol=1e-13)
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return dt, len(idx), min(threads, len(idx))  # OpenMP runs over nodes
+
+
+def reference_contour(wl):
+    """The contour the GPU arm places, restated on the host for the oracle: a single
+    ellipse from 0 to 1.05 x the spectral bound.  The bound comes from the free-field
+    formula scaled by the link roughness headroom (no GPU on this arm)."""
+    from oracle import contour, freefield
+
+    lo, hi = freefield.spectrum_bounds(tuple(reversed(wl["dims"])), M0)
+    R = 1.05 * hi * 1.05
+    return contour.single_contour(wl["n_q"], R / 2, R / 2, 0.25)
+
+
+def run_reference(args, wl):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    U, b = workload_inputs(wl, 0)
+    z, c, c0 = reference_contour(wl)
+    stride = max(1, wl["n_q"] // 16)  # 16 nodes per step: a bounded sample
+    for _ in range(args.warmup):
+        oracle_sample(U, b[0], z, c, c0, stride)
+    times = []
+    for _ in range(args.steps):
+        dt, nn, threads = oracle_sample(U, b[0], z, c, c0, stride)
+        times.append(dt * len(z) / nn)  # seconds per source apply, scaled to all nodes
+    per_apply = statistics.mean(times)
+    value = 1.0 / per_apply
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_apply * 1e3 * wl["nsrc"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(args, wl, "fp64"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"per step: source 0, {nn} of {len(z)} nodes (every {stride}th), per-node CGNR "
+                                   f"to 1e-13 and weighted sum; time scaled by {len(z)}/{nn}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(args, wl, mode):
+    return {
+        "workload": args.workload, "lattice": "x".join(map(str, wl["dims"])), "link_eps": wl["eps"], "m0": M0,
+        "r": 1.0, "bc_t": "antiperiodic", "m_q": wl["m_q"], "N_q": wl["n_q"], "sources_per_gpu": wl["nsrc"],
+        "source": "complex Gaussian" if wl["src"] == "gauss" else "spin-colour point sources",
+        "tol": wl["tol"], "mode": mode, "contour": "single ellipse placed from Lanczos bounds (setup, untimed)",
+        "l2": "256 MiB buffer written between timed steps", "parallelism": f"independent sources per GPU x{args.gpus}",
+    }
+
+
+# ------------------------------------------------------------------ ours
+
+def kernel_src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2204_01583_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(kernel, workload):
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(p) as f:
+            t = json.load(f)
+        e = t.get(f"{kernel}@{workload}")
+        if e and e.get("src_hash") == kernel_src_hash():
+            return e.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def run_ours(args, wl):
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2204_01583_gb300 import build as build_lib
+
+    build_lib()
+    from paper_2204_01583_gb300 import lib
+
+    mode = args.mode or wl["mode"]
+    U, b = workload_inputs(wl, rank)
+    nsrc = b.shape[0]
+    dev = torch.device("cuda", local)
+    ctx = lib.Context(wl["dims"], bc_t=-1, m0=M0, device=local)
+    ctx.set_gauge(torch.from_numpy(U).to(dev))
+    spec = ctx.place_contour(wl["n_q"], steps=150)
+    bd = torch.from_numpy(b).to(dev)
+    out = torch.empty_like(bd)
+    opts = ctx.opts(mode=mode, tol=wl["tol"])
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(o=opts, src=bd, dst=out):
+        return ctx.overlap(wl["m_q"], src, dst, nsrc, o)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    t_steps, stats = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats.append(step())
+        e1.record(stream)
+        e1.synchronize()
+        t_steps.append(e0.elapsed_time(e1))
+    barrier()
+    clocks = sampler.stop()
+    total_ms = sum(t_steps)
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    applies = nsrc * args.steps * world
+    value = applies / (total_ms / 1e3)
+
+    # end to end: the same call with pinned host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hb = torch.from_numpy(b).pin_memory()
+        ho = torch.empty_like(hb).pin_memory()
+        ho_opts = ctx.opts(mode=mode, tol=wl["tol"], host_io=True)
+        step(ho_opts, hb, ho)
+        barrier()
+        te = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.overlap(wl["m_q"], hb, ho, nsrc, ho_opts, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            te.append(e0.elapsed_time(e1))
+        barrier()
+        tot = sum(te)
+        if world > 1:
+            import torch.distributed as dist
+
+            t = torch.tensor([tot], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        nbytes = int(b.nbytes)
+        e2e = {"value": applies / (tot / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    # per-kernel durations (library events on the launching stream), K more steps
+    ctx.set_kernel_timing(True)
+    kstats = []
+    for _ in range(args.steps):
+        flush.zero_()
+        kstats.append(step())
+    torch.cuda.synchronize()
+    ktimes = ctx.kernel_times()
+    ctx.set_kernel_timing(False)
+    roof, kernels = roofline(wl, mode, ktimes, kstats, nsrc)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if mode != "mixed" else "f32+f64", "data": "synthetic",
+        "config": config_dict(args, wl, mode), "clocks": clocks, "e2e": e2e,
+        "gpu_launches": int(sum(s["launches"] for s in stats)), "roofline": roof, "kernels": kernels,
+        "solver": {"iterations": stats[-1]["iterations"], "max_residual": stats[-1]["max_residual"],
+                   "error_bound": stats[-1]["error_bound"], "converged": stats[-1]["converged"],
+                   "spectrum": spec},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        z, c, c0 = ctx.get_contour()
+        stride = max(1, wl["n_q"] // 16)
+        dt, nn, threads = oracle_sample(U, b[0], z, c, c0, stride)
+        per_apply = dt * len(z) / nn
+        line["cpu_baseline"] = {"value": 1.0 / per_apply, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"source 0, {nn} of {len(z)} nodes (every {stride}th), per-node CGNR to "
+                                          f"1e-13 and weighted sum; time scaled by {len(z)}/{nn}"}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def roofline(wl, mode, ktimes, kstats, nsrc):
+    """Achieved rate of each kernel class from algorithmic work and measured durations."""
+    V = int(np.prod(wl["dims"]))
+    upd = sum(s["node_updates"] for s in kstats)
+    iters = sum(s["iterations"] for s in kstats) * nsrc  # source-iterations (upper bound)
+    hbm, hbm_src = hbm_peak()
+    out = {}
+    if mode in ("fp64", "fp64_2pass"):
+        # lanczos_update_kernel: per node-update and site, p read+write (12 complex, FP64) and the
+        # weighted-sum FMA: 12 x 16 flops, 384 B; per source-iteration and site the Lanczos update
+        # (3 vectors, 48 B x 12 / 2 ...) counted as 12 x 10 flops, 12 x 64 B.
+        n_upd = ktimes.get("lanczos_update_kernel", (0, 0.0))
+        fl = 192.0 * upd * V + 120.0 * iters * V
+        by = 384.0 * upd * V + 768.0 * iters * V
+        if n_upd[0]:
+            out["lanczos_update_kernel"] = {"launches": n_upd[0], "ms": n_upd[1],
+                                            "tflops": fl / (n_upd[1] / 1e3) / 1e12,
+                                            "gbs": by / (n_upd[1] / 1e3) / 1e9}
+        # lanczos_hw_kernel: H_W stencil (1368 flops/site) + epilogue; 960 B/site FP64 compulsory
+        n_hw = ktimes.get("lanczos_hw_kernel", (0, 0.0))
+        fl_hw = (1368.0 + 72.0) * iters * V
+        by_hw = (960.0 + 2 * 192.0) * iters * V
+        if n_hw[0]:
+            out["lanczos_hw_kernel"] = {"launches": n_hw[0], "ms": n_hw[1],
+                                        "tflops": fl_hw / (n_hw[1] / 1e3) / 1e12,
+                                        "gbs": by_hw / (n_hw[1] / 1e3) / 1e9}
+    for k, (n, ms) in ktimes.items():
+        if n and k not in out:
+            out[k] = {"launches": n, "ms": ms}
+    if not out:
+        return None, out
+    dom = max(out, key=lambda k: out[k]["ms"])
+    d = out[dom]
+    if "tflops" in d:
+        roof = {"bound": "alu", "achieved": d["tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": d["tflops"] / FP64_PEAK_TFLOPS, "traffic": stored_traffic(dom, "default"),
+                "kernel": dom, "peak_source": "nominal FP64 of GB300 (profiling recipe)",
+                "hbm_gbs_algorithmic": d["gbs"], "hbm_frac_of_measured": d["gbs"] / hbm,
+                "launch_avg_us": d["ms"] / d["launches"] * 1e3}
+    else:
+        roof = {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None, "traffic": None,
+                "kernel": dom, "peak_source": hbm_src}
+    return roof, out
+
+
+def main():
+    args = parse()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

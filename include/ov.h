@@ -105,6 +105,9 @@ typedef struct {
   double error_bound;    /* max over sources of sum_j |c_j| r_j / |Im z_j| (relative to ||b||):
                             bound on ||S_N b - out|| / ||b|| because ||(z - H)^-1|| <= 1/|Im z| */
   double ms;             /* wall time of the call on the host, milliseconds                  */
+  double node_updates;   /* sum over iterations and sources of the nodes updated (the vector
+                            work of the shifted solve is proportional to it)                 */
+  double launches;       /* kernel launches the call enqueued (graph nodes included)          */
 } ov_stats;
 
 /* Spectral bounds from Lanczos (ov_place_contour). */

@@ -178,6 +178,8 @@ void fill_stats(ov_stats* st, const SolveOut& so, double ms) {
   st->max_residual = so.max_residual;
   st->error_bound = so.error_bound;
   st->ms = ms;
+  st->node_updates = so.node_updates;
+  st->launches = so.launches;
 }
 
 }  // namespace

@@ -141,6 +141,8 @@ struct SolveOut {
   double error_bound = 0.0;
   int refine_rounds = 0;
   int inner_iterations = 0;
+  double node_updates = 0.0;
+  double launches = 0.0;
 };
 int solve_sign_soa(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nrhs,
                    const ov_solve_opts& o, SolveOut* so, cudaStream_t s,

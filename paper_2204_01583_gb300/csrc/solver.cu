@@ -47,6 +47,7 @@ struct SrcState {
   int done;
   int status;     // OV_OK, OV_ERR_NOT_CONVERGED, OV_ERR_BREAKDOWN
   int n_act;
+  double node_updates;  // sum over iterations of n_act
 };
 
 struct ShiftState {
@@ -198,6 +199,7 @@ __global__ void __launch_bounds__(NT1) lanczos_hw_kernel(SolveArgs<R> a) {
     ++na;
   }
   S->n_act = na;
+  S->node_updates += na;
 }
 
 // K2: U_{i+1} = w - alpha_i U_i / n_i (in place over w), beta_i = ||U_{i+1}||,
@@ -350,6 +352,7 @@ __global__ void __launch_bounds__(NT2) lanczos_init_kernel(SolveArgs<R> a, const
   S->iter = 1;
   S->status = OV_OK;
   S->n_act = 0;
+  S->node_updates = 0.0;
   S->done = 0;
   const int ns = a.prm->nshift;
   for (int j = 0; j < ns; ++j) {
@@ -454,7 +457,7 @@ int launch_iteration(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, cudaStream_t s)
 // Run iterations until every source is done or max_iter is reached.
 template <typename R>
 int run_iterations(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, int nshift, int flavour, int max_iter,
-                   const ov_solve_opts& o, cudaStream_t s) {
+                   const ov_solve_opts& o, cudaStream_t s, double* launches) {
   const int chunk = o.check_every > 0 ? o.check_every : 32;
   const bool graph = o.use_graph && !ctx->timing;
   cudaGraphExec_t exec = nullptr;
@@ -493,6 +496,7 @@ int run_iterations(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, int nshift, int f
       OV_CHECK_LAUNCH(ctx, "lanczos kernels");
     }
     done_iters += n;
+    *launches += 2.0 * n;
     cudaError_t e = cudaMemcpyAsync(ctx->host_flag, w.a.done_count, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaMemcpyAsync(done)");
     e = cudaStreamSynchronize(s);
@@ -545,7 +549,9 @@ int finish_solve(ov_ctx* ctx, SolveWs<R>& w, int nsrc, int ns, const std::vector
   so->converged = 1;
   so->max_residual = 0.0;
   so->error_bound = 0.0;
+  so->node_updates = 0.0;
   for (int r = 0; r < nsrc; ++r) {
+    so->node_updates += S[r].node_updates;
     so->iterations = std::max(so->iterations, S[r].iter - 1);
     if (!S[r].done) S[r].status = OV_ERR_NOT_CONVERGED;
     if (S[r].status != OV_OK) {
@@ -584,9 +590,11 @@ int solve_sign_soa(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc
     }
   st = init_solve<double>(ctx, w, b_soa, nsrc, ns, zh, ch, ctx->c0, o.tol, o.max_iter, s);
   if (st != OV_OK) return st;
-  st = run_iterations<double>(ctx, w, nsrc, ns, xs_soa ? 1 : 0, o.max_iter, o, s);
+  double launches = 1.0 + (xs_soa ? 1.0 : 0.0);  // init (+ zeroing)
+  st = run_iterations<double>(ctx, w, nsrc, ns, xs_soa ? 1 : 0, o.max_iter, o, s, &launches);
   if (st != OV_OK) return st;
   st = finish_solve<double>(ctx, w, nsrc, ns, zh, ch, so, s);
+  so->launches = launches + 2.0;  // pack + unpack/epilogue issued by the caller
   // copy the weighted sum out even when not converged (best iterate)
   cudaError_t e = cudaMemcpyAsync(out_soa, w.a.sacc, sizeof(double2) * 12 * (size_t)ctx->g.V * nsrc,
                                   cudaMemcpyDeviceToDevice, s);

@@ -45,7 +45,8 @@ class SolveOpts(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("refine_rounds", ctypes.c_int),
                 ("inner_iterations", ctypes.c_int), ("converged", ctypes.c_int),
-                ("max_residual", ctypes.c_double), ("error_bound", ctypes.c_double), ("ms", ctypes.c_double)]
+                ("max_residual", ctypes.c_double), ("error_bound", ctypes.c_double), ("ms", ctypes.c_double),
+                ("node_updates", ctypes.c_double), ("launches", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
