@@ -57,7 +57,8 @@ typedef enum {
   OV_ERR_BREAKDOWN = 4,     /* a Krylov recurrence produced a non-finite scalar */
   OV_ERR_CUDA = 5,          /* a CUDA runtime call failed                      */
   OV_ERR_NO_GAUGE = 6,      /* ov_set_gauge has not been called                */
-  OV_ERR_NO_CONTOUR = 7     /* no contour set on the context                   */
+  OV_ERR_NO_CONTOUR = 7,    /* no contour set on the context                   */
+  OV_ERR_SCRATCH_TOO_SMALL = 8 /* ov_apply_HW_noalloc: the call needs more than its fixed scratch */
 } ov_status;
 
 typedef enum { OV_FP64 = 0, OV_FP32 = 1 } ov_precision;
@@ -190,6 +191,24 @@ int ov_overlap_vjp(ov_ctx* ctx, double m_q, const void* eta, const void* b, void
  * total ms) and returns the number of classes.  Disabled by default. */
 int ov_set_kernel_timing(ov_ctx* ctx, int enable);
 int ov_kernel_times(ov_ctx* ctx, const char** names, long long* launches, double* total_ms, int cap);
+
+/* out = H_W in without allocating device memory (FP64, canonical layouts; U, in and
+ * out are caller-owned device pointers on the current device).  The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc -- a code that hands
+ * all of HBM to its own pool up front, a framework whose allocator must not be
+ * bypassed, or work enqueued while a stream is being captured into a graph.  It
+ * needs no context.  Its staging buffers (structure-of-arrays copies of U, in and
+ * out) live in one fixed 16 MiB device array inside the library, which every GPU
+ * that loads the library holds until the process exits; a call needs
+ * 576 V + 384 V nrhs bytes (V = sites, each part rounded up to 256 B) and larger
+ * requests return OV_ERR_SCRATCH_TOO_SMALL.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture.  Every call on a device shares
+ * the one array: calls that overlap on the GPU (different streams, or different
+ * host threads) race and must be serialised by the caller.  Nothing in the array
+ * needs to start at zero: each call writes all it reads. */
+int ov_apply_HW_noalloc(const int dims[4], int bc_t, double m0, const double* U, const void* in, void* out,
+                        int nrhs, void* stream);
 
 /* Library version string. */
 const char* ov_version(void);

@@ -22,6 +22,7 @@ OV_ERR_BREAKDOWN = 4
 OV_ERR_CUDA = 5
 OV_ERR_NO_GAUGE = 6
 OV_ERR_NO_CONTOUR = 7
+OV_ERR_SCRATCH_TOO_SMALL = 8
 
 OV_FP64, OV_FP32 = 0, 1
 OV_MODE_FP64, OV_MODE_MIXED, OV_MODE_FP64_2PASS = 0, 1, 2
@@ -34,6 +35,7 @@ EXPORTS = (
     "ov_create", "ov_destroy", "ov_last_error", "ov_set_gauge", "ov_apply_HW", "ov_set_contour",
     "ov_set_contour_ellipse", "ov_get_contour", "ov_place_contour", "ov_sgn_HW_apply", "ov_overlap_apply",
     "ov_sgn_vjp", "ov_overlap_vjp", "ov_set_kernel_timing", "ov_kernel_times", "ov_version",
+    "ov_apply_HW_noalloc",
 )
 
 
@@ -83,6 +85,7 @@ def _load():
         "ov_overlap_vjp": [vp, d, vp, vp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), vp],
         "ov_set_kernel_timing": [vp, i],
         "ov_kernel_times": [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong), dp, i],
+        "ov_apply_HW_noalloc": [ip, i, d, vp, vp, vp, i, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -249,6 +252,13 @@ class Context:
         ms = (ctypes.c_double * cap)()
         n = _lib.ov_kernel_times(self._h, names, launches, ms, cap)
         return {names[k].decode(): (int(launches[k]), float(ms[k])) for k in range(n)}
+
+
+def apply_HW_noalloc(dims, bc_t, m0, U, psi_in, psi_out, nrhs, stream=None):
+    """ov_apply_HW_noalloc: FP64 H_W on device tensors without any allocation in the
+    library (fixed internal scratch).  Returns the ov_status code."""
+    return _lib.ov_apply_HW_noalloc((ctypes.c_int * 4)(*[int(x) for x in dims]), int(bc_t), float(m0), _ptr(U),
+                                    _ptr(psi_in), _ptr(psi_out), int(nrhs), _stream_ptr(stream))
 
 
 def version():
