@@ -377,49 +377,59 @@ def run_ours(args, wl):
     return 0
 
 
+# Algorithmic work per unit for each kernel class (FP64): (flops, bytes).
+# Units: "si" = source-iteration x site, "nu" = node-update x site.
+#   lanczos_hw_kernel:     H_W stencil 1368 flop + epilogue 72 flop; links 576 B + U_i, U_{i-1}
+#                          read and w written (3 x 192 B)                      per si
+#   lanczos_update_kernel: U_{i+1} = w - alpha v (12 x 10 flop; 3 x 192 B)    per si
+#                          + p = v - l p and s += c zeta p (12 x 16 flop; p read+write 384 B) per nu
+#   lanczos_regen_kernel:  stencil + Lanczos update + s += g v (1368 + 12 x 24 flop;
+#                          576 + 4 x 192 B + sum read+write 384 B)            per si
+FP64_WORK = {
+    "lanczos_hw_kernel": {"si": (1440.0, 1152.0)},
+    "lanczos_update_kernel": {"si": (120.0, 576.0), "nu": (192.0, 384.0)},
+    "lanczos_regen_kernel": {"si": (1656.0, 1728.0)},
+}
+
+
 def roofline(wl, mode, ktimes, kstats, nsrc):
     """Achieved rate of each kernel class from algorithmic work and measured durations."""
     V = int(np.prod(wl["dims"]))
-    upd = sum(s["node_updates"] for s in kstats)
-    iters = sum(s["iterations"] for s in kstats) * nsrc  # source-iterations (upper bound)
+    units = {"nu": sum(s["node_updates"] for s in kstats) * V,
+             "si": sum(s["iterations"] for s in kstats) * nsrc * V}  # source-iterations (upper bound)
     hbm, hbm_src = hbm_peak()
     out = {}
-    if mode in ("fp64", "fp64_2pass"):
-        # lanczos_update_kernel: per node-update and site, p read+write (12 complex, FP64) and the
-        # weighted-sum FMA: 12 x 16 flops, 384 B; per source-iteration and site the Lanczos update
-        # (3 vectors, 48 B x 12 / 2 ...) counted as 12 x 10 flops, 12 x 64 B.
-        n_upd = ktimes.get("lanczos_update_kernel", (0, 0.0))
-        fl = 192.0 * upd * V + 120.0 * iters * V
-        by = 384.0 * upd * V + 768.0 * iters * V
-        if n_upd[0]:
-            out["lanczos_update_kernel"] = {"launches": n_upd[0], "ms": n_upd[1],
-                                            "tflops": fl / (n_upd[1] / 1e3) / 1e12,
-                                            "gbs": by / (n_upd[1] / 1e3) / 1e9}
-        # lanczos_hw_kernel: H_W stencil (1368 flops/site) + epilogue; 960 B/site FP64 compulsory
-        n_hw = ktimes.get("lanczos_hw_kernel", (0, 0.0))
-        fl_hw = (1368.0 + 72.0) * iters * V
-        by_hw = (960.0 + 2 * 192.0) * iters * V
-        if n_hw[0]:
-            out["lanczos_hw_kernel"] = {"launches": n_hw[0], "ms": n_hw[1],
-                                        "tflops": fl_hw / (n_hw[1] / 1e3) / 1e12,
-                                        "gbs": by_hw / (n_hw[1] / 1e3) / 1e9}
     for k, (n, ms) in ktimes.items():
-        if n and k not in out:
-            out[k] = {"launches": n, "ms": ms}
+        if not n:
+            continue
+        d = {"launches": n, "ms": ms, "avg_us": ms / n * 1e3}
+        if mode in ("fp64", "fp64_2pass") and k in FP64_WORK:
+            fl = sum(units[u] * w[0] for u, w in FP64_WORK[k].items())
+            by = sum(units[u] * w[1] for u, w in FP64_WORK[k].items())
+            d["tflops"] = fl / (ms / 1e3) / 1e12
+            d["gbs"] = by / (ms / 1e3) / 1e9
+        out[k] = d
     if not out:
         return None, out
     dom = max(out, key=lambda k: out[k]["ms"])
     d = out[dom]
     if "tflops" in d:
         roof = {"bound": "alu", "achieved": d["tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": d["tflops"] / FP64_PEAK_TFLOPS, "traffic": stored_traffic(dom, "default"),
-                "kernel": dom, "peak_source": "nominal FP64 of GB300 (profiling recipe)",
+                "frac": d["tflops"] / FP64_PEAK_TFLOPS, "traffic": stored_traffic(dom, wl_name_of(wl)),
+                "kernel": dom, "peak_source": "nominal FP64 of GB300 (profiling recipe); an FMA loop measures 1.20",
                 "hbm_gbs_algorithmic": d["gbs"], "hbm_frac_of_measured": d["gbs"] / hbm,
-                "launch_avg_us": d["ms"] / d["launches"] * 1e3}
+                "launch_avg_us": d["avg_us"]}
     else:
         roof = {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None, "traffic": None,
                 "kernel": dom, "peak_source": hbm_src}
     return roof, out
+
+
+def wl_name_of(wl):
+    for k, v in WORKLOADS.items():
+        if v is wl:
+            return k
+    return "?"
 
 
 def main():

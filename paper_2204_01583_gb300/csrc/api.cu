@@ -11,7 +11,7 @@
 
 const char* const kKernelClassNames[KC_COUNT] = {"hw_kernel",         "lanczos_hw_kernel", "lanczos_update_kernel",
                                                   "layout_kernels",    "init_kernels",      "force_kernel",
-                                                  "residual_kernels"};
+                                                  "residual_kernels",  "lanczos_regen_kernel"};
 
 // ------------------------------------------------------------ utilities
 
@@ -160,8 +160,10 @@ int sign_core(ov_ctx* ctx, const double2* b_dev, int nrhs, const ov_solve_opts& 
   if (st != OV_OK) return st;
   st = launch_pack64(ctx, b_dev, b_soa, nrhs, s);
   if (st != OV_OK) return st;
-  if (o.mode == OV_MODE_FP64) {
+  if (o.mode == OV_MODE_FP64 || xs) {
     st = solve_sign_soa(ctx, b_soa, s_soa, nrhs, o, so, s, xs);
+  } else if (o.mode == OV_MODE_FP64_2PASS) {
+    st = solve_sign_2pass(ctx, b_soa, s_soa, nrhs, o, so, s);
   } else {
     return ctx_fail(ctx, OV_ERR_INVALID_ARG, "solver mode not available in this build");
   }

@@ -201,3 +201,59 @@ __device__ __forceinline__ double sum_partials(const double* p, int n, double* s
   for (int i = threadIdx.x; i < n; i += NT) v += __ldcg(p + i);
   return block_sum<NT>(v, sh);
 }
+
+// ------------------------------------------------- stencil, 4 threads per site
+// A block of 128 threads handles 32 consecutive sites.  Phase 1: warp w computes the
+// two hops of direction mu = w for the 32 sites (consecutive lanes, consecutive
+// sites) and writes its 12 partial components to shared memory.  Phase 2: thread t
+// owns site site0 + (t & 31) and components 3 (t >> 5) .. 3 (t >> 5) + 2 and adds
+// the diagonal term, the four partials and gamma5.  Four times the threads of
+// hw_site for the same work, for small lattices where one thread per site leaves
+// most of the GPU idle.  sm must hold 4 * 12 * 32 complex numbers.
+constexpr int kSplitNT = 128;
+constexpr int kSplitSites = 32;
+
+template <typename R>
+__device__ __forceinline__ void hw_split_phase1(const typename Store<R>::T* __restrict__ in,
+                                                const typename Store<R>::T* __restrict__ U, const Geom& g,
+                                                int site0, Cx<R>* sm) {
+  const int lane = threadIdx.x & 31, mu = threadIdx.x >> 5;
+  const int s = site0 + lane;
+  Cx<R> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
+  if (s < g.V) {
+    int c[4];
+    site_coords(g, s, c);
+    switch (mu) {  // warp-uniform
+      case 0: hop_dir<0, R>(in, U, g, s, c, acc); break;
+      case 1: hop_dir<1, R>(in, U, g, s, c, acc); break;
+      case 2: hop_dir<2, R>(in, U, g, s, c, acc); break;
+      default: hop_dir<3, R>(in, U, g, s, c, acc); break;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) sm[(mu * 12 + k) * kSplitSites + lane] = acc[k];
+}
+
+// Phase 2 for this thread's three components kk = 3 (t >> 5) + {0, 1, 2}; call after
+// __syncthreads().  Returns false for sites beyond V.
+template <typename R>
+__device__ __forceinline__ bool hw_split_phase2(const typename Store<R>::T* __restrict__ in, const Geom& g,
+                                                int site0, R diag, const Cx<R>* sm, Cx<R> o[3], int* s_out,
+                                                int* k0_out) {
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int s = site0 + lane;
+  *s_out = s;
+  *k0_out = 3 * grp;
+  if (s >= g.V) return false;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int k = 3 * grp + q;
+    Cx<R> v = cscale(diag, ld<R>(in + k * (size_t)g.V + s));
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) v = cadd(v, sm[(mu * 12 + k) * kSplitSites + lane]);
+    o[q] = (k >= 6) ? cneg(v) : v;
+  }
+  return true;
+}

@@ -47,6 +47,7 @@ enum KernelClass {
   KC_MISC,           // initialisation and small kernels
   KC_FORCE,          // link force
   KC_RESIDUAL,       // FP64 true residuals (mixed mode)
+  KC_REGEN,          // second pass of the two-pass mode
   KC_COUNT
 };
 
@@ -147,6 +148,10 @@ struct SolveOut {
 int solve_sign_soa(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nrhs,
                    const ov_solve_opts& o, SolveOut* so, cudaStream_t s,
                    double2* xs_soa /* optional per-node solutions [src][node][12V] */);
+
+// two-pass FP64 variant (OV_MODE_FP64_2PASS)
+int solve_sign_2pass(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nrhs, const ov_solve_opts& o,
+                     SolveOut* so, cudaStream_t s);
 
 // Lanczos on H (or H^2) for spectral bounds (solver.cu); fills alpha[0..k), beta[0..k)
 int lanczos_tridiag(ov_ctx* ctx, int steps, int squared, std::vector<double>& alpha,

@@ -27,7 +27,9 @@
 // the block partials in a fixed order, so reruns are bit-identical, and updates the
 // scalars.  The host only reads a done counter every few iterations, and replays
 // the per-iteration kernels from a CUDA graph.
+#include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <vector>
 
@@ -35,7 +37,7 @@
 
 namespace {
 
-constexpr int NT1 = 128;  // K1: stencil + Lanczos epilogue
+constexpr int NT1 = 128;  // K1: stencil + Lanczos epilogue; K3: regeneration pass
 constexpr int NT2 = 256;  // K2: vector updates
 
 struct SrcState {
@@ -48,6 +50,8 @@ struct SrcState {
   int status;     // OV_OK, OV_ERR_NOT_CONVERGED, OV_ERR_BREAKDOWN
   int n_act;
   double node_updates;  // sum over iterations of n_act
+  int k_final;    // second pass: number of Lanczos vectors to regenerate
+  int pad_;
 };
 
 struct ShiftState {
@@ -61,6 +65,7 @@ struct SolveParams {
   double tol;
   int max_iter;
   int nshift;
+  int vec_shifts;  // 1: per-node direction vectors and the weighted sum in K2; 0: scalars only
 };
 
 // Device pointers of one solve (all in workspace owned by the context).
@@ -86,6 +91,7 @@ struct SolveArgs {
   int* done_count;
   double* hist_a;     // [src][max_iter] or null
   double* hist_b;
+  const double2* gco; // [src][max_iter] second-pass coefficients or null
   const SolveParams* prm;
   const T* U;         // links
   Geom g;
@@ -100,18 +106,72 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// The Lanczos vector arithmetic, written with explicitly rounded operations so that
+// every kernel that performs it (K1/K2 of the solve, K3 of the second pass) produces
+// the same bits: the second pass of OV_MODE_FP64_2PASS regenerates the first pass's
+// basis exactly.
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// w = (H U_i) / n_i - (n_i / n_{i-1}) U_{i-1}   (second term absent at i = 1)
+template <typename R>
+__device__ __forceinline__ Cx<R> lz_w(Cx<R> o, Cx<R> um, R inv_n, R cm, bool first) {
+  Cx<R> w = {rmul(inv_n, o.re), rmul(inv_n, o.im)};
+  if (!first) {
+    w.re = rfma(-cm, um.re, w.re);
+    w.im = rfma(-cm, um.im, w.im);
+  }
+  return w;
+}
+// v_i = U_i / n_i
+template <typename R>
+__device__ __forceinline__ Cx<R> lz_v(Cx<R> u, R inv_n) {
+  return {rmul(inv_n, u.re), rmul(inv_n, u.im)};
+}
+// U_{i+1} = w - alpha_i v_i
+template <typename R>
+__device__ __forceinline__ Cx<R> lz_next(Cx<R> w, Cx<R> v, R alpha) {
+  return {rfma(-alpha, v.re, w.re), rfma(-alpha, v.im, w.im)};
+}
+
 __device__ void mark_done(SrcState* S, int* done_count, int status) {
   S->done = 1;
   S->status = status;
   atomicAdd(done_count, 1);
 }
 
-// K1: w = H U_i / n_i - (n_i / n_{i-1}) U_{i-1};  alpha_i = Re <U_i, w> / n_i.
+// Block-wide ordered compaction helper: returns this thread's slot among the
+// threads with flag set (in thread order) and the block total in *total.
+template <int NT>
+__device__ __forceinline__ int block_rank(bool flag, int* total, int* wsh) {
+  const unsigned bal = __ballot_sync(0xffffffffu, flag);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) wsh[wid] = __popc(bal);
+  __syncthreads();
+  int off = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < NT / 32; ++w) {
+    if (w < wid) off += wsh[w];
+    tot += wsh[w];
+  }
+  __syncthreads();
+  *total = tot;
+  return off + __popc(bal & ((1u << lane) - 1u));
+}
+
+// K1: w = H U_i / n_i - (n_i / n_{i-1}) U_{i-1};  alpha_i = Re <U_i, w> / n_i; then,
+// in the last block, row i of every active node's LDL^T and the active list for K2.
+// The stencil runs 4 threads per site (hw_split_*): a block covers 32 sites.
 template <typename R>
 __global__ void __launch_bounds__(NT1) lanczos_hw_kernel(SolveArgs<R> a) {
   using T = typename Store<R>::T;
   __shared__ double sh[NT1 / 32];
+  __shared__ int wsh[NT1 / 32];
   __shared__ bool last;
+  __shared__ double alpha_sh;
+  __shared__ Cx<R> sm[4 * 12 * kSplitSites];
   const int r = blockIdx.y;
   SrcState* S = a.src + r;
   if (S->done) return;
@@ -124,28 +184,38 @@ __global__ void __launch_bounds__(NT1) lanczos_hw_kernel(SolveArgs<R> a) {
   T* W = base + (size_t)((i + 1) % 3) * n12;
   const double inv_n = 1.0 / S->n_cur;
   const double cm = (i > 1) ? S->n_cur / S->n_prev : 0.0;
-  const int s = blockIdx.x * NT1 + threadIdx.x;
+  const int site0 = blockIdx.x * kSplitSites;
   double dot = 0.0;
-  if (s < V) {
-    Cx<R> o[12];
-    if (a.stencil) {
+  if (a.stencil) {
+    // pre-applied operator (H^2 Lanczos for the spectral gap): one thread per (site, 3 components)
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5, s = site0 + lane;
+    if (s < V) {
       const T* Hs = a.stencil + (size_t)r * n12;
 #pragma unroll
-      for (int k = 0; k < 12; ++k) o[k] = ld<R>(Hs + k * (size_t)V + s);
-    } else {
-      hw_site<R>(Ui, a.U, a.g, s, a.diag, o);
-    }
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      const size_t e = k * (size_t)V + s;
-      Cx<R> u = ld<R>(Ui + e);
-      Cx<R> w = cscale((R)inv_n, o[k]);
-      if (i > 1) {
-        Cx<R> um = ld<R>(Um + e);
-        w = csub(w, cscale((R)cm, um));
+      for (int q = 0; q < 3; ++q) {
+        const size_t e = (3 * grp + q) * (size_t)V + s;
+        const Cx<R> u = ld<R>(Ui + e);
+        const Cx<R> um = (i > 1) ? ld<R>(Um + e) : Cx<R>{R(0), R(0)};
+        const Cx<R> w = lz_w<R>(ld<R>(Hs + e), um, (R)inv_n, (R)cm, i == 1);
+        st<R>(W + e, w);
+        dot += (double)u.re * (double)w.re + (double)u.im * (double)w.im;
       }
-      st<R>(W + e, w);
-      dot += (double)u.re * (double)w.re + (double)u.im * (double)w.im;
+    }
+  } else {
+    hw_split_phase1<R>(Ui, a.U, a.g, site0, sm);
+    __syncthreads();
+    Cx<R> o[3];
+    int s, k0;
+    if (hw_split_phase2<R>(Ui, a.g, site0, a.diag, sm, o, &s, &k0)) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const size_t e = (k0 + q) * (size_t)V + s;
+        const Cx<R> u = ld<R>(Ui + e);
+        const Cx<R> um = (i > 1) ? ld<R>(Um + e) : Cx<R>{R(0), R(0)};
+        const Cx<R> w = lz_w<R>(o[q], um, (R)inv_n, (R)cm, i == 1);
+        st<R>(W + e, w);
+        dot += (double)u.re * (double)w.re + (double)u.im * (double)w.im;
+      }
     }
   }
   double bs = block_sum<NT1>(dot, sh);
@@ -157,58 +227,76 @@ __global__ void __launch_bounds__(NT1) lanczos_hw_kernel(SolveArgs<R> a) {
   __syncthreads();
   if (!last) return;
   __threadfence();
-  double tot = sum_partials<NT1>(a.part1 + (size_t)r * gridDim.x, gridDim.x, sh);
-  if (threadIdx.x != 0) return;
-  a.cnt[2 * r] = 0;
-  const double alpha = tot * inv_n;
-  S->alpha = alpha;
-  if (a.hist_a) a.hist_a[(size_t)r * a.prm->max_iter + (i - 1)] = alpha;
-  if (!isfinite(alpha)) {
-    S->n_act = 0;
-    mark_done(S, a.done_count, OV_ERR_BREAKDOWN);
-    return;
+  const double tot = sum_partials<NT1>(a.part1 + (size_t)r * gridDim.x, gridDim.x, sh);
+  if (threadIdx.x == 0) {
+    a.cnt[2 * r] = 0;
+    const double alpha = tot * inv_n;
+    S->alpha = alpha;
+    alpha_sh = alpha;
+    if (a.hist_a) a.hist_a[(size_t)r * a.prm->max_iter + (i - 1)] = alpha;
+    if (!isfinite(alpha)) {
+      S->n_act = 0;
+      mark_done(S, a.done_count, OV_ERR_BREAKDOWN);
+    }
   }
-  // per-node LDL^T row i and the active list for K2
+  __syncthreads();
+  const double alpha = alpha_sh;
+  if (!isfinite(alpha)) return;
+  // per-node LDL^T row i (one thread per node) and the ordered active list
   const int ns = a.prm->nshift;
   const double beta_prev = S->n_cur;  // beta_{i-1} = ||U_i|| (i >= 2)
   int na = 0;
-  for (int j = 0; j < ns; ++j) {
-    ShiftState& q = a.sh[(size_t)r * ns + j];
-    if (!q.active) continue;
-    const double2 zj = a.z[(size_t)r * ns + j];
-    double2 d, om;
-    double2 lprev = make_double2(0.0, 0.0);
-    if (i == 1) {
-      d = make_double2(zj.x - alpha, zj.y);
-      om = make_double2(S->bnorm, 0.0);
-    } else {
-      const double2 t = cdiv(make_double2(beta_prev * beta_prev, 0.0), q.d);
-      d = make_double2(zj.x - alpha - t.x, zj.y - t.y);
-      lprev = q.l;
-      om = cmul(make_double2(-lprev.x, -lprev.y), q.omega);
+  for (int j0 = 0; j0 < ns; j0 += NT1) {
+    const int j = j0 + threadIdx.x;
+    bool act = false;
+    double2 lprev = make_double2(0.0, 0.0), zeta = make_double2(0.0, 0.0);
+    if (j < ns) {
+      ShiftState& q = a.sh[(size_t)r * ns + j];
+      act = q.active != 0;
+      if (act) {
+        const double2 zj = a.z[(size_t)r * ns + j];
+        double2 d, om;
+        if (i == 1) {
+          d = make_double2(zj.x - alpha, zj.y);
+          om = make_double2(S->bnorm, 0.0);
+        } else {
+          const double2 t = cdiv(make_double2(beta_prev * beta_prev, 0.0), q.d);
+          d = make_double2(zj.x - alpha - t.x, zj.y - t.y);
+          lprev = q.l;
+          om = cmul(make_double2(-lprev.x, -lprev.y), q.omega);
+        }
+        zeta = cdiv(om, d);
+        q.d = d;
+        q.omega = om;
+        q.zeta = zeta;
+      }
     }
-    const double2 zeta = cdiv(om, d);
-    q.d = d;
-    q.omega = om;
-    q.zeta = zeta;
-    const size_t o = (size_t)r * ns + na;
-    a.act_idx[o] = j;
-    a.act_l[o] = lprev;
-    a.act_cz[o] = cmul(a.c[(size_t)r * ns + j], zeta);
-    a.act_z[o] = zeta;
-    ++na;
+    int cnt;
+    const int slot = block_rank<NT1>(act, &cnt, wsh);
+    if (act) {
+      const size_t o = (size_t)r * ns + na + slot;
+      a.act_idx[o] = j;
+      a.act_l[o] = lprev;
+      a.act_cz[o] = cmul(a.c[(size_t)r * ns + j], zeta);
+      a.act_z[o] = zeta;
+    }
+    na += cnt;
   }
-  S->n_act = na;
-  S->node_updates += na;
+  if (threadIdx.x == 0) {
+    S->n_act = na;
+    S->node_updates += (a.prm->vec_shifts ? na : 0);
+  }
 }
 
 // K2: U_{i+1} = w - alpha_i U_i / n_i (in place over w), beta_i = ||U_{i+1}||,
-// per active node p = v_i - l_{i-1} p, x += zeta_i p, s += c_j zeta_i p.
+// per active node p = v_i - l_{i-1} p, x += zeta_i p, s += c_j zeta_i p (vec_shifts),
+// then per-node residuals |beta_i zeta_i| and l_i = -beta_i / d_i in the last block.
 template <typename R>
 __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
   using T = typename Store<R>::T;
   __shared__ double sh[NT2 / 32];
   __shared__ bool last;
+  __shared__ double beta_sh;
   const int r = blockIdx.y;
   SrcState* S = a.src + r;
   if (S->done) return;
@@ -221,13 +309,12 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
   T* W = base + (size_t)((i + 1) % 3) * n12;
   const double inv_n = 1.0 / S->n_cur;
   const double alpha = S->alpha;
-  const int na = S->n_act;
+  const int na = a.prm->vec_shifts ? S->n_act : 0;
   const size_t e = (size_t)blockIdx.x * NT2 + threadIdx.x;
   double nrm = 0.0;
   if (e < n12) {
-    Cx<R> v = cscale((R)inv_n, ld<R>(Ui + e));
-    Cx<R> w = ld<R>(W + e);
-    Cx<R> u = csub(w, cscale((R)alpha, v));
+    const Cx<R> v = lz_v<R>(ld<R>(Ui + e), (R)inv_n);
+    const Cx<R> u = lz_next<R>(ld<R>(W + e), v, (R)alpha);
     st<R>(W + e, u);
     nrm = (double)u.re * (double)u.re + (double)u.im * (double)u.im;
     double sre = 0.0, sim = 0.0;
@@ -241,7 +328,7 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
       Cx<R> pv = v;
       if (i > 1) {
         const double2 l = __ldg(al + k);
-        Cx<R> po = ld<R>(P);
+        const Cx<R> po = ld<R>(P);
         pv.re = v.re - ((R)l.x * po.re - (R)l.y * po.im);
         pv.im = v.im - ((R)l.x * po.im + (R)l.y * po.re);
       }
@@ -275,30 +362,39 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
   __syncthreads();
   if (!last) return;
   __threadfence();
-  double tot = sum_partials<NT2>(a.part2 + (size_t)r * gridDim.x, gridDim.x, sh);
-  if (threadIdx.x != 0) return;
-  a.cnt[2 * r + 1] = 0;
-  const double beta = sqrt(tot);
-  if (a.hist_b) a.hist_b[(size_t)r * a.prm->max_iter + (i - 1)] = beta;
-  if (!isfinite(beta)) {
-    mark_done(S, a.done_count, OV_ERR_BREAKDOWN);
-    return;
+  const double tot = sum_partials<NT2>(a.part2 + (size_t)r * gridDim.x, gridDim.x, sh);
+  if (threadIdx.x == 0) {
+    a.cnt[2 * r + 1] = 0;
+    beta_sh = sqrt(tot);
+    if (a.hist_b) a.hist_b[(size_t)r * a.prm->max_iter + (i - 1)] = beta_sh;
+    if (!isfinite(beta_sh)) mark_done(S, a.done_count, OV_ERR_BREAKDOWN);
   }
+  __syncthreads();
+  const double beta = beta_sh;
+  if (!isfinite(beta)) return;
   const double tol = a.prm->tol;
+  const double bnorm = S->bnorm;
   int still = 0;
-  for (int j = 0; j < ns; ++j) {
-    ShiftState& q = a.sh[(size_t)r * ns + j];
-    if (!q.active) continue;
-    q.res = beta * sqrt(q.zeta.x * q.zeta.x + q.zeta.y * q.zeta.y) / S->bnorm;
-    q.l = cdiv(make_double2(-beta, 0.0), q.d);
-    q.last_iter = i;
-    if (q.res <= tol || beta == 0.0) {
-      q.active = 0;
-      if (beta == 0.0) q.res = 0.0;
-    } else {
-      ++still;
+  for (int j0 = 0; j0 < ns; j0 += NT2) {
+    const int j = j0 + threadIdx.x;
+    bool act = false;
+    if (j < ns) {
+      ShiftState& q = a.sh[(size_t)r * ns + j];
+      if (q.active) {
+        q.res = beta * sqrt(q.zeta.x * q.zeta.x + q.zeta.y * q.zeta.y) / bnorm;
+        q.l = cdiv(make_double2(-beta, 0.0), q.d);
+        q.last_iter = i;
+        if (q.res <= tol || beta == 0.0) {
+          q.active = 0;
+          if (beta == 0.0) q.res = 0.0;
+        } else {
+          act = true;
+        }
+      }
     }
+    still += __syncthreads_count(act);
   }
+  if (threadIdx.x != 0) return;
   S->n_prev = S->n_cur;
   S->n_cur = beta;
   S->iter = i + 1;
@@ -308,6 +404,63 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
     mark_done(S, a.done_count, OV_OK);
   } else if (i >= a.prm->max_iter) {
     mark_done(S, a.done_count, ns > 0 ? OV_ERR_NOT_CONVERGED : OV_OK);
+  }
+}
+
+// K3 (second pass of OV_MODE_FP64_2PASS): regenerate U_{i+1} from the recorded
+// alpha_i and ||U_i|| with the first pass's arithmetic, and add g_i v_i to the sum.
+// One kernel per iteration; the last block advances the iteration counter.
+template <typename R>
+__global__ void __launch_bounds__(NT1) lanczos_regen_kernel(SolveArgs<R> a) {
+  using T = typename Store<R>::T;
+  __shared__ bool last;
+  __shared__ Cx<R> sm[4 * 12 * kSplitSites];
+  const int r = blockIdx.y;
+  SrcState* S = a.src + r;
+  const int i = S->iter;
+  if (i > S->k_final) return;
+  const int V = a.g.V;
+  const size_t n12 = (size_t)12 * V;
+  const int mi = a.prm->max_iter;
+  T* base = a.ring + (size_t)r * 3 * n12;
+  const T* Ui = base + (size_t)(i % 3) * n12;
+  const T* Um = base + (size_t)((i + 2) % 3) * n12;
+  T* W = base + (size_t)((i + 1) % 3) * n12;
+  const double n_i = (i == 1) ? S->bnorm : a.hist_b[(size_t)r * mi + i - 2];
+  const double n_m = (i <= 2) ? S->bnorm : a.hist_b[(size_t)r * mi + i - 3];
+  const double inv_n = 1.0 / n_i;
+  const double cm = (i > 1) ? n_i / n_m : 0.0;
+  const double alpha = a.hist_a[(size_t)r * mi + i - 1];
+  const double2 g = a.gco[(size_t)r * mi + i - 1];
+  const int site0 = blockIdx.x * kSplitSites;
+  hw_split_phase1<R>(Ui, a.U, a.g, site0, sm);
+  __syncthreads();
+  Cx<R> o[3];
+  int s, k0;
+  if (hw_split_phase2<R>(Ui, a.g, site0, a.diag, sm, o, &s, &k0)) {
+    double2* Sx = a.sacc + (size_t)r * n12 + s;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int k = k0 + q;
+      const size_t e = k * (size_t)V + s;
+      const Cx<R> um = (i > 1) ? ld<R>(Um + e) : Cx<R>{R(0), R(0)};
+      const Cx<R> w = lz_w<R>(o[q], um, (R)inv_n, (R)cm, i == 1);
+      const Cx<R> v = lz_v<R>(ld<R>(Ui + e), (R)inv_n);
+      st<R>(W + e, lz_next<R>(w, v, (R)alpha));
+      double2 sv = Sx[k * (size_t)V];
+      sv.x += g.x * (double)v.re - g.y * (double)v.im;
+      sv.y += g.x * (double)v.im + g.y * (double)v.re;
+      Sx[k * (size_t)V] = sv;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = (atomicAdd(a.cnt + 2 * r, 1u) == gridDim.x - 1);
+    if (last) {
+      a.cnt[2 * r] = 0;
+      S->iter = i + 1;
+    }
   }
 }
 
@@ -353,6 +506,7 @@ __global__ void __launch_bounds__(NT2) lanczos_init_kernel(SolveArgs<R> a, const
   S->status = OV_OK;
   S->n_act = 0;
   S->node_updates = 0.0;
+  S->k_final = 0;
   S->done = 0;
   const int ns = a.prm->nshift;
   for (int j = 0; j < ns; ++j) {
@@ -368,6 +522,22 @@ __global__ void __launch_bounds__(NT2) lanczos_init_kernel(SolveArgs<R> a, const
       a.sh[(size_t)r * ns + j].res = 0.0;
     }
     mark_done(S, a.done_count, isfinite(S->bnorm) ? OV_OK : OV_ERR_BREAKDOWN);
+  }
+}
+
+// second pass: U_1 = b again in ring slot 1 (the first pass overwrote the ring)
+template <typename R>
+__global__ void ring_reset_kernel(SolveArgs<R> a, const double2* __restrict__ b, int nsrc) {
+  using T = typename Store<R>::T;
+  const size_t n12 = (size_t)12 * a.g.V;
+  const size_t n = n12 * nsrc;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = t / n12, e = t % n12;
+    const double2 bv = b[t];
+    T v;
+    v.x = bv.x;
+    v.y = bv.y;
+    a.ring[r * 3 * n12 + n12 + e] = v;
   }
 }
 
@@ -404,7 +574,7 @@ int setup_ws(ov_ctx* ctx, int nsrc, int ns, bool want_x, bool want_sacc, bool wa
   const size_t n12 = (size_t)12 * V;
   int st = OV_OK;
   std::string t(tag);
-  w->nblk1 = (V + NT1 - 1) / NT1;
+  w->nblk1 = (V + kSplitSites - 1) / kSplitSites;
   w->nblk2 = (int)((n12 + NT2 - 1) / NT2);
   auto& a = w->a;
   a.ring = (T*)ws_get(ctx, (t + ".ring").c_str(), sizeof(T) * 3 * n12 * nsrc, &st);
@@ -430,6 +600,7 @@ int setup_ws(ov_ctx* ctx, int nsrc, int ns, bool want_x, bool want_sacc, bool wa
   } else {
     a.hist_a = a.hist_b = nullptr;
   }
+  a.gco = nullptr;
   w->prm_dev = (SolveParams*)ws_get(ctx, (t + ".prm").c_str(), sizeof(SolveParams), &st);
   a.prm = w->prm_dev;
   a.stencil = nullptr;
@@ -510,8 +681,8 @@ int run_iterations(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, int nshift, int f
 template <typename R>
 int init_solve(ov_ctx* ctx, SolveWs<R>& w, const double2* b_soa, int nsrc, int ns,
                const std::vector<double2>& zh, const std::vector<double2>& ch, double2 c0,
-               double tol, int max_iter, cudaStream_t s) {
-  SolveParams prm{tol, max_iter, ns};
+               double tol, int max_iter, cudaStream_t s, int vec_shifts = 1) {
+  SolveParams prm{tol, max_iter, ns, vec_shifts};
   cudaError_t e = cudaMemcpyAsync(w.prm_dev, &prm, sizeof(prm), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy params");
   if (ns > 0) {
@@ -600,6 +771,139 @@ int solve_sign_soa(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc
                                   cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy sum");
   return st;
+}
+
+// OV_MODE_FP64_2PASS.  Pass 1: the Lanczos process with every node's LDL^T scalar
+// recurrence (for the stopping test) but no per-node vectors; alpha_i and beta_i
+// are recorded.  Host: for every node the FOM coefficients y^j = (z_j - T_k)^-1 e_1 ||b||
+// (forward LDL^T sweep, back substitution), summed as g = sum_j c_j y^j.  Pass 2:
+// regenerate v_1 .. v_k with bit-identical arithmetic and accumulate
+// s = c0 b + sum_i g_i v_i.  Same result as OV_MODE_FP64 up to rounding; the vector
+// work no longer grows with the number of nodes.
+int solve_sign_2pass(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc, const ov_solve_opts& o,
+                     SolveOut* so, cudaStream_t s) {
+  const int ns = (int)ctx->z.size();
+  SolveWs<double> w;
+  int st = setup_ws<double>(ctx, nsrc, ns, false, true, true, o.max_iter, &w, "fp64");
+  if (st != OV_OK) return st;
+  double2* gco = (double2*)ws_get(ctx, "fp64.gco", sizeof(double2) * (size_t)nsrc * o.max_iter, &st);
+  if (st != OV_OK) return st;
+  w.a.p = nullptr;
+  std::vector<double2> zh((size_t)nsrc * ns), ch((size_t)nsrc * ns);
+  for (int r = 0; r < nsrc; ++r)
+    for (int j = 0; j < ns; ++j) {
+      zh[(size_t)r * ns + j] = ctx->z[j];
+      ch[(size_t)r * ns + j] = ctx->c[j];
+    }
+  st = init_solve<double>(ctx, w, b_soa, nsrc, ns, zh, ch, ctx->c0, o.tol, o.max_iter, s, 0);
+  if (st != OV_OK) return st;
+  double launches = 1.0;
+  st = run_iterations<double>(ctx, w, nsrc, ns, 2, o.max_iter, o, s, &launches);
+  if (st != OV_OK) return st;
+  const int fst = finish_solve<double>(ctx, w, nsrc, ns, zh, ch, so, s);
+  if (fst != OV_OK && fst != OV_ERR_NOT_CONVERGED) return fst;
+  // coefficients of the sum in the Lanczos basis
+  std::vector<SrcState> S(nsrc);
+  cudaError_t e = cudaMemcpyAsync(S.data(), w.a.src, sizeof(SrcState) * nsrc, cudaMemcpyDeviceToHost, s);
+  std::vector<double> ha((size_t)nsrc * o.max_iter), hb((size_t)nsrc * o.max_iter);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ha.data(), w.a.hist_a, sizeof(double) * ha.size(), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hb.data(), w.a.hist_b, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "read Lanczos history");
+  std::vector<double2> g((size_t)nsrc * o.max_iter, make_double2(0.0, 0.0));
+  int kmax = 0;
+  std::vector<std::complex<double>> dd, ll, zt, yy;
+  for (int r = 0; r < nsrc; ++r) {
+    const int k = S[r].iter - 1;
+    S[r].k_final = k;
+    kmax = std::max(kmax, k);
+    if (k < 1) continue;
+    const double* al = ha.data() + (size_t)r * o.max_iter;
+    const double* be = hb.data() + (size_t)r * o.max_iter;
+    dd.assign(k, 0.0);
+    ll.assign(k, 0.0);
+    zt.assign(k, 0.0);
+    yy.assign(k, 0.0);
+    for (int j = 0; j < ns; ++j) {
+      const std::complex<double> zj(ctx->z[j].x, ctx->z[j].y), cj(ctx->c[j].x, ctx->c[j].y);
+      std::complex<double> om = S[r].bnorm;
+      for (int i = 0; i < k; ++i) {
+        if (i == 0) {
+          dd[0] = zj - al[0];
+        } else {
+          dd[i] = zj - al[i] - be[i - 1] * be[i - 1] / dd[i - 1];
+          om = -ll[i - 1] * om;
+        }
+        ll[i] = -be[i] / dd[i];
+        zt[i] = om / dd[i];
+      }
+      yy[k - 1] = zt[k - 1];
+      for (int i = k - 2; i >= 0; --i) yy[i] = zt[i] - ll[i] * yy[i + 1];
+      for (int i = 0; i < k; ++i) {
+        const std::complex<double> t = cj * yy[i];
+        g[(size_t)r * o.max_iter + i].x += t.real();
+        g[(size_t)r * o.max_iter + i].y += t.imag();
+      }
+    }
+    S[r].iter = 1;
+    S[r].done = 0;
+  }
+  e = cudaMemcpyAsync(gco, g.data(), sizeof(double2) * g.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w.a.src, S.data(), sizeof(SrcState) * nsrc, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.a.cnt, 0, sizeof(unsigned) * 2 * nsrc, s);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "second-pass setup");
+  w.a.gco = gco;
+  ring_reset_kernel<double><<<256, 256, 0, s>>>(w.a, b_soa, nsrc);
+  launches += 1.0;
+  // pass 2: kmax regeneration launches (no host reads), replayed from a graph
+  const int chunk = o.check_every > 0 ? o.check_every : 32;
+  const bool graph = o.use_graph && !ctx->timing;
+  cudaGraphExec_t exec = nullptr;
+  if (graph && kmax >= chunk) {
+    GraphKey key{{(const void*)w.a.ring, (const void*)gco, (const void*)w.a.sacc, (const void*)w.a.hist_a},
+                 nsrc, ns, 3, chunk};
+    auto it = ctx->graphs.find(key);
+    if (it != ctx->graphs.end()) {
+      exec = it->second;
+    } else {
+      cudaError_t ce = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (ce != cudaSuccess) return ctx_cuda(ctx, ce, "cudaStreamBeginCapture");
+      for (int k = 0; k < chunk; ++k)
+        lanczos_regen_kernel<double><<<dim3(w.nblk1, nsrc), NT1, 0, ctx->cap_stream>>>(w.a);
+      cudaGraph_t gph = nullptr;
+      ce = cudaStreamEndCapture(ctx->cap_stream, &gph);
+      if (ce != cudaSuccess) return ctx_cuda(ctx, ce, "cudaStreamEndCapture");
+      ce = cudaGraphInstantiate(&exec, gph, 0);
+      cudaGraphDestroy(gph);
+      if (ce != cudaSuccess) return ctx_cuda(ctx, ce, "cudaGraphInstantiate");
+      ctx->graphs[key] = exec;
+    }
+  }
+  int done = 0;
+  while (done < kmax) {
+    const int n = std::min(chunk, kmax - done);
+    if (exec && n == chunk) {
+      e = cudaGraphLaunch(exec, s);
+      if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaGraphLaunch");
+    } else {
+      for (int k = 0; k < n; ++k) {
+        cudaEvent_t ev;
+        kt_begin(ctx, KC_REGEN, s, &ev);
+        lanczos_regen_kernel<double><<<dim3(w.nblk1, nsrc), NT1, 0, s>>>(w.a);
+        kt_end(ctx, KC_REGEN, s, ev);
+      }
+      OV_CHECK_LAUNCH(ctx, "lanczos_regen_kernel");
+    }
+    done += n;
+    launches += n;
+  }
+  so->launches = launches + 2.0;
+  e = cudaMemcpyAsync(out_soa, w.a.sacc, sizeof(double2) * 12 * (size_t)ctx->g.V * nsrc,
+                      cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy sum");
+  return fst;
 }
 
 // Lanczos tridiagonal of H_W (squared = 0) or H_W^2 (squared = 1) from a fixed

@@ -23,14 +23,15 @@ def _oracle(U, b, ctx, tol=1e-13):
     return out
 
 
-def test_config1_4x4_dense(gpu_lib):
+@pytest.mark.parametrize("mode", ["fp64", "fp64_2pass"])
+def test_config1_4x4_dense(gpu_lib, mode):
     """4^4, eps = 0.3, N_q = 32 from Lanczos placement: parity with the per-node oracle,
     accuracy vs dense zheevd sgn, GW relation and sgn^2 = 1 within the predicted error."""
     dims = (4, 4, 4, 4)
     ctx, U = make_ctx(gpu_lib, dims, 0.3, S.seed_for("config1"))
     spec = ctx.place_contour(32, steps=120)
     b = S.gaussian_spinor(dims, S.seed_for("config1.b"))
-    got, st = sgn_gpu(ctx, b, tol=1e-12)
+    got, st = sgn_gpu(ctx, b, tol=1e-12, mode=mode)
     assert st["converged"] == 1
     want = _oracle(U, b, ctx)
     assert rel(got, want) < PARITY
@@ -53,41 +54,62 @@ def test_config1_4x4_dense(gpu_lib):
 
     Sb = to_dev(got)
     S2b = torch.empty_like(Sb)
-    ctx.sgn(Sb, S2b, 1)
+    ctx.sgn(Sb, S2b, 1, ctx.opts(mode=mode))
     s2 = to_host(S2b)
     assert np.linalg.norm(s2 - b) / np.linalg.norm(b) <= 2.01 * method_err + 1e-10
     assert sign.sigma(b, got) <= 2.01 * method_err + 1e-10
 
 
-def test_config2_8x4_parity(gpu_lib):
-    """8^4, eps = 0.5, N_q = 64, tol 1e-12: 4 sources in one call; one source against the
-    per-node CGNR oracle at 1e-10, all four: sgn^2 b = b within the predicted method error."""
-    import torch
-
+@pytest.fixture(scope="module")
+def config2(gpu_lib):
+    """8^4, eps = 0.5, N_q = 64 (Lanczos placement), 4 Gaussian sources; oracle for source 0."""
     dims = (8, 8, 8, 8)
     ctx, U = make_ctx(gpu_lib, dims, 0.5, S.seed_for("config2"))
     spec = ctx.place_contour(64, steps=150)
     b = S.gaussian_spinor(dims, S.seed_for("config2.b"), n=4)
-    got, st = sgn_gpu(ctx, b, nrhs=4, tol=1e-12)
+    want0 = _oracle(U, b[0], ctx)
+    return ctx, U, b, spec, want0
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp64_2pass"])
+def test_config2_8x4_parity(gpu_lib, config2, mode):
+    """tol 1e-12, 4 sources in one call; source 0 against the per-node CGNR oracle at 1e-10,
+    all four: sgn^2 b = b within the predicted method error."""
+    import torch
+
+    ctx, U, b, spec, want0 = config2
+    got, st = sgn_gpu(ctx, b, nrhs=4, tol=1e-12, mode=mode)
     assert st["converged"] == 1 and st["max_residual"] <= 1e-12
-    want = _oracle(U, b[0], ctx)
-    assert rel(got[0], want) < PARITY
-    # sgn^2 = 1 on all four sources
+    assert rel(got[0], want0) < PARITY
     S2 = torch.empty_like(to_dev(got))
-    ctx.sgn(to_dev(got), S2, 4)
+    ctx.sgn(to_dev(got), S2, 4, ctx.opts(mode=mode))
     s2 = to_host(S2)
     for k in range(4):
         assert rel(s2[k], b[k]) < max(10 * spec["predicted_error"], 1e-9)
 
 
-def test_ragged_lattice_parity(gpu_lib):
-    """Lattice whose volume is not a multiple of any block size."""
+def test_two_pass_equals_shifted(gpu_lib, config2):
+    """The coefficient-space two-pass form and the vector-space shifted form compute the
+    same Galerkin iterates: agreement to rounding, per source."""
+    ctx, U, b, spec, want0 = config2
+    a, sa = sgn_gpu(ctx, b, nrhs=4, tol=1e-12, mode="fp64")
+    c, sc = sgn_gpu(ctx, b, nrhs=4, tol=1e-12, mode="fp64_2pass")
+    assert sa["iterations"] == sc["iterations"]
+    for k in range(4):
+        assert rel(c[k], a[k]) < 1e-12
+    assert sc["node_updates"] == 0 and sa["node_updates"] > 0
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp64_2pass"])
+def test_ragged_lattice_parity(gpu_lib, mode):
+    """Lattice whose volume is not a multiple of any block size; 3 sources."""
     dims = (3, 5, 4, 6)
     ctx, U = make_ctx(gpu_lib, dims, 0.5, 51)
     ctx.set_contour_ellipse(24, 3.4, 3.4, 0.3)
-    b = S.gaussian_spinor(dims, 52)
-    got, st = sgn_gpu(ctx, b, tol=1e-12)
-    assert rel(got, _oracle(U, b, ctx)) < PARITY
+    b = S.gaussian_spinor(dims, 52, n=3)
+    got, st = sgn_gpu(ctx, b, tol=1e-12, mode=mode)
+    for k in range(3):
+        assert rel(got[k], _oracle(U, b[k], ctx)) < PARITY
 
 
 def test_free_field_closed_form_8x4(gpu_lib):
@@ -149,27 +171,33 @@ def test_graph_and_direct_launch_agree_bitwise(gpu_lib):
     assert np.array_equal(a1, a2)
 
 
-def test_edge_cases(gpu_lib):
+@pytest.mark.parametrize("mode", ["fp64", "fp64_2pass"])
+def test_edge_cases(gpu_lib, mode):
     import torch
 
     dims = (4, 4, 4, 4)
     ctx, U = make_ctx(gpu_lib, dims, 0.3, 95)
     ctx.set_contour_ellipse(16, 3.4, 3.4, 0.3)
     # zero source -> zero output
-    z0, st = sgn_gpu(ctx, np.zeros(S.lattice_shape(dims) + (4, 3), np.complex128))
+    z0, st = sgn_gpu(ctx, np.zeros(S.lattice_shape(dims) + (4, 3), np.complex128), mode=mode)
     assert np.all(z0 == 0) and st["converged"] == 1
     # iteration cap -> NOT_CONVERGED, output holds the current iterate
     b = S.gaussian_spinor(dims, 96)
     bd = to_dev(b)
     out = torch.empty_like(bd)
-    st = ctx.sgn(bd, out, 1, ctx.opts(max_iter=3), allow_not_converged=True)
+    st = ctx.sgn(bd, out, 1, ctx.opts(max_iter=3, mode=mode), allow_not_converged=True)
     assert st["status"] == gpu_lib.OV_ERR_NOT_CONVERGED and st["converged"] == 0
     # NaN in the source -> BREAKDOWN status, no hang
     bn = b.copy()
     bn[0, 0, 0, 0, 0, 0] = np.nan
     with pytest.raises(gpu_lib.OvError) as e:
-        sgn_gpu(ctx, bn)
+        sgn_gpu(ctx, bn, mode=mode)
     assert e.value.code == gpu_lib.OV_ERR_BREAKDOWN
+    # a zero source next to a nonzero one in the same call
+    bz = np.stack([np.zeros_like(b), b])
+    mixed, _ = sgn_gpu(ctx, bz, nrhs=2, mode=mode)
+    alone, _ = sgn_gpu(ctx, b, mode=mode)
+    assert np.all(mixed[0] == 0) and np.array_equal(mixed[1], alone)
     # nrhs = 0 is a no-op
     ctx.sgn(bd, out, 0)
     # bad options
