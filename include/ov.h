@@ -185,6 +185,17 @@ int ov_sgn_vjp(ov_ctx* ctx, const void* eta, const void* b, void* grad_b, double
 int ov_overlap_vjp(ov_ctx* ctx, double m_q, const void* eta, const void* b, void* grad_b,
                    double* grad_links, const ov_solve_opts* opts, ov_stats* stats, void* stream);
 
+/* FP32 stencil selection for ov_apply_HW(OV_FP32) and the FP32 phases of the mixed
+ * solve.  Variants differ in right-hand sides per thread (link loads reused across
+ * them), 12-real link compression (row 2 rebuilt as conj(row0 x row1)) and block
+ * size.  k = -1 (default): autotune -- each variant is timed once on the live data per
+ * right-hand-side count and the fastest is kept.  ov_hw32_variants returns the number
+ * of variants and, for 0 <= k < count, describes variant k; the last one
+ * (compressed = 2) is the right-hand-side-paired layout computed with paired FP32
+ * instructions and broadcast links. */
+int ov_set_hw32_variant(ov_ctx* ctx, int k);
+int ov_hw32_variants(int k, int* rhs_tile, int* compressed, int* threads);
+
 /* Kernel timing: when enabled, the library brackets every launch of its main
  * kernel classes with CUDA events on the launching stream and accumulates their
  * durations.  ov_kernel_times fills up to `cap` entries (name pointer, launches,

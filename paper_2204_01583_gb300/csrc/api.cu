@@ -278,6 +278,8 @@ int ov_set_gauge(ov_ctx* ctx, const double* U, int on_device, void* stream) {
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "ov_set_gauge");
   kt_collect(ctx);
   ctx->have_gauge = true;
+  ctx->have_c32 = false;
+  ctx->have_b32 = false;
   return OV_OK;
 }
 
@@ -300,12 +302,49 @@ int ov_apply_HW(ov_ctx* ctx, const void* in, void* out, int nrhs, int precision,
     if ((st = launch_hw64(ctx, a, b, nrhs, s))) return st;
     if ((st = launch_unpack64(ctx, b, (double2*)out, nrhs, s))) return st;
   } else {
+    const int npair = (nrhs + 1) / 2;
+    const int kpair = hw32_variant_count();
     float2* a = (float2*)ws_get(ctx, "hw.a32", sizeof(float2) * n, &st);
     float2* b = (float2*)ws_get(ctx, "hw.b32", sizeof(float2) * n, &st);
+    float4* pa = (float4*)ws_get(ctx, "hw.pa32", sizeof(float4) * 12 * (size_t)ctx->g.V * npair, &st);
+    float4* pb = (float4*)ws_get(ctx, "hw.pb32", sizeof(float4) * 12 * (size_t)ctx->g.V * npair, &st);
     if (st != OV_OK) return st;
-    if ((st = launch_pack32(ctx, (const float2*)in, a, nrhs, s))) return st;
-    if ((st = launch_hw32(ctx, a, b, nrhs, s))) return st;
-    if ((st = launch_unpack32(ctx, b, (float2*)out, nrhs, s))) return st;
+    int k = ctx->hw32_force;
+    if (k < 0) {
+      auto it = ctx->hw32_choice.find(nrhs);
+      if (it != ctx->hw32_choice.end()) {
+        k = it->second;
+      } else {
+        // autotune: every structure-of-arrays variant and the paired kernel, on this data
+        if ((st = launch_pack32(ctx, (const float2*)in, a, nrhs, s))) return st;
+        int ksoa = 0;
+        const float soa_ms = hw32_time_soa_variants(ctx, a, b, nrhs, s, &ksoa);
+        if ((st = launch_pack_pair32(ctx, (const float2*)in, pa, nrhs, s))) return st;
+        if ((st = launch_hw_pair(ctx, pa, pb, npair, s))) return st;  // warm (builds the links)
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, s);
+        for (int rep = 0; rep < 3; ++rep) launch_hw_pair(ctx, pa, pb, npair, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float pms = 0.f;
+        cudaEventElapsedTime(&pms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        k = (pms / 3 < soa_ms) ? kpair : ksoa;
+        ctx->hw32_choice[nrhs] = k;
+      }
+    }
+    if (k == kpair) {
+      if ((st = launch_pack_pair32(ctx, (const float2*)in, pa, nrhs, s))) return st;
+      if ((st = launch_hw_pair(ctx, pa, pb, npair, s))) return st;
+      if ((st = launch_unpack_pair32(ctx, pb, (float2*)out, nrhs, s))) return st;
+    } else {
+      if ((st = launch_pack32(ctx, (const float2*)in, a, nrhs, s))) return st;
+      if ((st = launch_hw32_tuned(ctx, a, b, nrhs, s, k, nullptr))) return st;
+      if ((st = launch_unpack32(ctx, b, (float2*)out, nrhs, s))) return st;
+    }
   }
   return OV_OK;
 }
@@ -484,6 +523,24 @@ int ov_overlap_vjp(ov_ctx* ctx, double m_q, const void* eta, const void* b, void
                    const ov_solve_opts* opts, ov_stats* stats, void* stream) {
   (void)m_q; (void)eta; (void)b; (void)grad_b; (void)grad_links; (void)opts; (void)stats; (void)stream;
   return ctx_fail(ctx, OV_ERR_INVALID_ARG, "ov_overlap_vjp is not available in this build");
+}
+
+int ov_set_hw32_variant(ov_ctx* ctx, int k) {
+  if (!ctx) return OV_ERR_INVALID_ARG;
+  if (k < -1 || k > hw32_variant_count()) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "no such FP32 stencil variant");
+  ctx->hw32_force = k;
+  return OV_OK;
+}
+
+int ov_hw32_variants(int k, int* rhs_tile, int* compressed, int* threads) {
+  const int n = hw32_variant_count();
+  if (k >= 0 && k < n && rhs_tile && compressed && threads) hw32_variant_info(k, rhs_tile, compressed, threads);
+  if (k == n && rhs_tile && compressed && threads) {  // paired layout, FFMA2, broadcast links
+    *rhs_tile = 2;
+    *compressed = 2;
+    *threads = 128;
+  }
+  return n + 1;
 }
 
 int ov_set_kernel_timing(ov_ctx* ctx, int enable) {

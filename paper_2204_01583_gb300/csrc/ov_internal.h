@@ -77,6 +77,10 @@ struct ov_ctx {
   double2* U64 = nullptr;
   float2* U32 = nullptr;
   bool have_gauge = false;
+  bool have_c32 = false;               // compressed FP32 links (workspace "gauge.c32") are current
+  bool have_b32 = false;               // broadcast FP32 links for the paired layout ("gauge.b32")
+  std::map<int, int> hw32_choice;      // nrhs -> autotuned FP32 stencil variant
+  int hw32_force = -1;                 // ov_set_hw32_variant
 
   // quadrature S_N = c0 + sum_j c_j (z_j - H)^-1
   std::vector<double2> z, c;
@@ -128,6 +132,17 @@ int launch_unpack32(ov_ctx* ctx, const float2* soa, float2* aos, int nrhs, cudaS
 // out (SoA) = H_W in (SoA)
 int launch_hw64(ov_ctx* ctx, const double2* in, double2* out, int nrhs, cudaStream_t s);
 int launch_hw32(ov_ctx* ctx, const float2* in, float2* out, int nrhs, cudaStream_t s);
+// FP32 multi-RHS stencil (dslash32.cu): variant -1 = autotuned
+int launch_hw32_tuned(ov_ctx* ctx, const float2* in, float2* out, int nrhs, cudaStream_t s, int force_variant,
+                      int* used);
+int hw32_variant_count();  // SoA variants; index hw32_variant_count() is the paired kernel
+void hw32_variant_info(int k, int* rt, int* comp, int* nt);
+float hw32_time_soa_variants(ov_ctx* ctx, const float2* in, float2* out, int nrhs, cudaStream_t s, int* best);
+// paired FP32 layout (pair32.cu)
+const float4* pair_links(ov_ctx* ctx, cudaStream_t s, int* st);
+int launch_pack_pair32(ov_ctx* ctx, const float2* aos, float4* pr, int nrhs, cudaStream_t s);
+int launch_unpack_pair32(ov_ctx* ctx, const float4* pr, float2* aos, int nrhs, cudaStream_t s);
+int launch_hw_pair(ov_ctx* ctx, const float4* in, float4* out, int npair, cudaStream_t s);
 // out(AoS) = (1+m)/2 b(AoS) + (1-m)/2 gamma5 s(SoA)
 int launch_overlap_epilogue(ov_ctx* ctx, const double2* b_aos, const double2* s_soa, double2* out_aos,
                             double m_q, int nrhs, cudaStream_t s);

@@ -35,7 +35,7 @@ EXPORTS = (
     "ov_create", "ov_destroy", "ov_last_error", "ov_set_gauge", "ov_apply_HW", "ov_set_contour",
     "ov_set_contour_ellipse", "ov_get_contour", "ov_place_contour", "ov_sgn_HW_apply", "ov_overlap_apply",
     "ov_sgn_vjp", "ov_overlap_vjp", "ov_set_kernel_timing", "ov_kernel_times", "ov_version",
-    "ov_apply_HW_noalloc",
+    "ov_apply_HW_noalloc", "ov_set_hw32_variant", "ov_hw32_variants",
 )
 
 
@@ -86,6 +86,8 @@ def _load():
         "ov_set_kernel_timing": [vp, i],
         "ov_kernel_times": [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong), dp, i],
         "ov_apply_HW_noalloc": [ip, i, d, vp, vp, vp, i, vp],
+        "ov_set_hw32_variant": [vp, i],
+        "ov_hw32_variants": [i, ip, ip, ip],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -241,6 +243,9 @@ class Context:
         self._check(rc)
         return st.as_dict()
 
+    def set_hw32_variant(self, k=-1):
+        self._check(_lib.ov_set_hw32_variant(self._h, int(k)))
+
     # ------------------------------------------------------------------ timing
     def set_kernel_timing(self, enable=True):
         self._check(_lib.ov_set_kernel_timing(self._h, int(bool(enable))))
@@ -259,6 +264,17 @@ def apply_HW_noalloc(dims, bc_t, m0, U, psi_in, psi_out, nrhs, stream=None):
     library (fixed internal scratch).  Returns the ov_status code."""
     return _lib.ov_apply_HW_noalloc((ctypes.c_int * 4)(*[int(x) for x in dims]), int(bc_t), float(m0), _ptr(U),
                                     _ptr(psi_in), _ptr(psi_out), int(nrhs), _stream_ptr(stream))
+
+
+def hw32_variants():
+    """[(rhs_tile, compressed, threads)] of the FP32 stencil variants."""
+    n = _lib.ov_hw32_variants(-1, None, None, None)
+    out = []
+    for k in range(n):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _lib.ov_hw32_variants(k, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        out.append((a.value, b.value, c.value))
+    return out
 
 
 def version():

@@ -80,3 +80,37 @@ def test_hw_rejects_bad_arguments(gpu_lib):
     with pytest.raises(gpu_lib.OvError) as e:
         ctx2.apply_HW(x, y, 1, gpu_lib.OV_FP64)  # no gauge
     assert e.value.code == gpu_lib.OV_ERR_NO_GAUGE
+
+
+@pytest.mark.parametrize("variant", list(range(9)))
+def test_hw_fp32_variants(gpu_lib, variant):
+    """Every FP32 stencil variant (RHS tile, link compression, block size) against the
+    oracle, with a right-hand-side count that leaves a ragged last tile."""
+    import torch
+
+    assert len(gpu_lib.hw32_variants()) == 9
+    dims = (6, 4, 5, 4)
+    ctx, U = make_ctx(gpu_lib, dims, 0.6, 71)
+    ctx.set_hw32_variant(variant)
+    nrhs = 7
+    psi = S.gaussian_spinor(dims, 72, n=nrhs).astype(np.complex64)
+    out = torch.empty(psi.shape, dtype=torch.complex64, device="cuda")
+    ctx.apply_HW(to_dev(psi), out, nrhs, gpu_lib.OV_FP32)
+    got = to_host(out).astype(np.complex128)
+    for k in range(nrhs):
+        want = cimpl.hw_apply(U, psi[k].astype(np.complex128), M0)
+        assert rel(got[k], want) < 3e-6
+
+
+def test_hw_fp32_autotuned_12rhs_16x32(gpu_lib):
+    import torch
+
+    dims = (16, 16, 16, 32)
+    ctx, U = make_ctx(gpu_lib, dims, 0.6, 81)
+    nrhs = 12
+    psi = S.gaussian_spinor(dims, 82, n=nrhs).astype(np.complex64)
+    out = torch.empty(psi.shape, dtype=torch.complex64, device="cuda")
+    ctx.apply_HW(to_dev(psi), out, nrhs, gpu_lib.OV_FP32)
+    got = to_host(out).astype(np.complex128)
+    for k in (0, 11):
+        assert rel(got[k], cimpl.hw_apply(U, psi[k].astype(np.complex128), M0)) < 3e-6
