@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variant", type=int, default=None, help="dslash workloads: time only this FP32 stencil variant")
+    ap.add_argument("--compare-steps", type=int, default=2,
+                    help="mixed workloads: steps of each plain FP64 form timed for the comparison")
     return ap.parse_args()
 
 
@@ -363,6 +365,9 @@ def run_ours(args, wl):
                    "error_bound": stats[-1]["error_bound"], "converged": stats[-1]["converged"],
                    "spectrum": spec},
     }
+    if mode == "mixed" and args.compare_steps > 0:
+        line["mixed_vs_fp64"] = compare_fp64(ctx, wl, bd, out, nsrc, stream, flush, args.compare_steps,
+                                             total_ms / args.steps)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         z, c, c0 = ctx.get_contour()
         stride = max(1, wl["n_q"] // 16)
@@ -394,6 +399,37 @@ FP64_WORK = {
     "lanczos_update_kernel": {"si": (120.0, 576.0), "nu": (192.0, 384.0)},
     "lanczos_regen_kernel": {"si": (1656.0, 1728.0)},
 }
+
+
+def compare_fp64(ctx, wl, bd, out_mixed, nsrc, stream, flush, steps, mixed_ms):
+    """Same step with the plain FP64 forms: time per step, speed-up of the mixed form and
+    the largest relative difference per source between the mixed and FP64 results."""
+    import torch
+
+    res = {"mixed_ms_per_step": mixed_ms}
+    ref = None
+    for mode in ("fp64", "fp64_2pass"):
+        o = ctx.opts(mode=mode, tol=wl["tol"])
+        ob = torch.empty_like(bd)
+        ctx.overlap(wl["m_q"], bd, ob, nsrc, o)  # warm-up
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.overlap(wl["m_q"], bd, ob, nsrc, o)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = sum(ts) / len(ts)
+        res[f"{mode}_ms_per_step"] = ms
+        res[f"speedup_vs_{mode}"] = ms / mixed_ms
+        if ref is None:
+            ref = ob
+    d = (out_mixed - ref).reshape(nsrc, -1).norm(dim=1) / ref.reshape(nsrc, -1).norm(dim=1)
+    res["max_rel_diff_vs_fp64"] = float(d.max().item())
+    return res
 
 
 def roofline(wl, mode, ktimes, kstats, nsrc):

@@ -164,6 +164,8 @@ int sign_core(ov_ctx* ctx, const double2* b_dev, int nrhs, const ov_solve_opts& 
     st = solve_sign_soa(ctx, b_soa, s_soa, nrhs, o, so, s, xs);
   } else if (o.mode == OV_MODE_FP64_2PASS) {
     st = solve_sign_2pass(ctx, b_soa, s_soa, nrhs, o, so, s);
+  } else if (o.mode == OV_MODE_MIXED) {
+    st = solve_sign_mixed(ctx, b_soa, s_soa, nrhs, o, so, s);
   } else {
     return ctx_fail(ctx, OV_ERR_INVALID_ARG, "solver mode not available in this build");
   }

@@ -168,6 +168,18 @@ int solve_sign_soa(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nrhs
 int solve_sign_2pass(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nrhs, const ov_solve_opts& o,
                      SolveOut* so, cudaStream_t s);
 
+// mixed-precision variant (OV_MODE_MIXED) and its kernels (mixed.cu)
+int solve_sign_mixed(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nrhs, const ov_solve_opts& o,
+                     SolveOut* so, cudaStream_t s);
+int launch_basis_combine(ov_ctx* ctx, const float2* basis, int nslots, const float2* W, int kmax, const int* kr,
+                         double2* Y, int nsrc, int nq, cudaStream_t s);
+int launch_residual64(ov_ctx* ctx, const double2* Y, const double2* b, const double2* z, double2* R, double* part,
+                      double* rnorm2, int nsrc, int nq, cudaStream_t s);
+int residual64_partials(ov_ctx* ctx);
+int launch_accumulate(ov_ctx* ctx, double2* Y, const float2* X, size_t n, cudaStream_t s);
+int launch_weighted_sum(ov_ctx* ctx, const double2* Y, const double2* b, const double2* c, double2 c0, double2* out,
+                        int nsrc, int nq, cudaStream_t s);
+
 // Lanczos on H (or H^2) for spectral bounds (solver.cu); fills alpha[0..k), beta[0..k)
 int lanczos_tridiag(ov_ctx* ctx, int steps, int squared, std::vector<double>& alpha,
                     std::vector<double>& beta, cudaStream_t s);

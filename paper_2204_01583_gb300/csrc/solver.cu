@@ -30,6 +30,8 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstdio>
+#include <string>
 #include <cstring>
 #include <vector>
 
@@ -66,6 +68,8 @@ struct SolveParams {
   int max_iter;
   int nshift;
   int vec_shifts;  // 1: per-node direction vectors and the weighted sum in K2; 0: scalars only
+  int nslots;      // Lanczos vector slots per source: 3 (ring, slot i % 3) or a stored basis (slot i)
+  int store;       // 1: slot i holds U_i for every i (basis kept for a later combination)
 };
 
 // Device pointers of one solve (all in workspace owned by the context).
@@ -92,6 +96,7 @@ struct SolveArgs {
   double* hist_a;     // [src][max_iter] or null
   double* hist_b;
   const double2* gco; // [src][max_iter] second-pass coefficients or null
+  const double* tol_src;  // [src] per-source tolerance or null (then SolveParams::tol)
   const SolveParams* prm;
   const T* U;         // links
   Geom g;
@@ -104,6 +109,11 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Lanczos vector slot of iteration index i: a ring of three, or the stored basis.
+__device__ __forceinline__ size_t lz_slot(const SolveParams* p, int i) {
+  return p->store ? (size_t)i : (size_t)(i % 3);
 }
 
 // The Lanczos vector arithmetic, written with explicitly rounded operations so that
@@ -178,10 +188,10 @@ __global__ void __launch_bounds__(NT1) lanczos_hw_kernel(SolveArgs<R> a) {
   const int V = a.g.V;
   const size_t n12 = (size_t)12 * V;
   const int i = S->iter;
-  T* base = a.ring + (size_t)r * 3 * n12;
-  const T* Ui = base + (size_t)(i % 3) * n12;
-  const T* Um = base + (size_t)((i + 2) % 3) * n12;
-  T* W = base + (size_t)((i + 1) % 3) * n12;
+  T* base = a.ring + (size_t)r * a.prm->nslots * n12;
+  const T* Ui = base + lz_slot(a.prm, i) * n12;
+  const T* Um = base + (a.prm->store ? (size_t)(i - 1) : (size_t)((i + 2) % 3)) * n12;  // U_{i-1}
+  T* W = base + lz_slot(a.prm, i + 1) * n12;
   const double inv_n = 1.0 / S->n_cur;
   const double cm = (i > 1) ? S->n_cur / S->n_prev : 0.0;
   const int site0 = blockIdx.x * kSplitSites;
@@ -304,9 +314,9 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
   const size_t n12 = (size_t)12 * V;
   const int i = S->iter;
   const int ns = a.prm->nshift;
-  T* base = a.ring + (size_t)r * 3 * n12;
-  const T* Ui = base + (size_t)(i % 3) * n12;
-  T* W = base + (size_t)((i + 1) % 3) * n12;
+  T* base = a.ring + (size_t)r * a.prm->nslots * n12;
+  const T* Ui = base + lz_slot(a.prm, i) * n12;
+  T* W = base + lz_slot(a.prm, i + 1) * n12;
   const double inv_n = 1.0 / S->n_cur;
   const double alpha = S->alpha;
   const int na = a.prm->vec_shifts ? S->n_act : 0;
@@ -372,7 +382,7 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
   __syncthreads();
   const double beta = beta_sh;
   if (!isfinite(beta)) return;
-  const double tol = a.prm->tol;
+  const double tol = a.tol_src ? a.tol_src[r] : a.prm->tol;
   const double bnorm = S->bnorm;
   int still = 0;
   for (int j0 = 0; j0 < ns; j0 += NT2) {
@@ -402,7 +412,7 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
     mark_done(S, a.done_count, OV_OK);
   } else if (ns > 0 && still == 0) {
     mark_done(S, a.done_count, OV_OK);
-  } else if (i >= a.prm->max_iter) {
+  } else if (i >= a.prm->max_iter || (a.prm->store && i + 2 >= a.prm->nslots)) {
     mark_done(S, a.done_count, ns > 0 ? OV_ERR_NOT_CONVERGED : OV_OK);
   }
 }
@@ -422,7 +432,7 @@ __global__ void __launch_bounds__(NT1) lanczos_regen_kernel(SolveArgs<R> a) {
   const int V = a.g.V;
   const size_t n12 = (size_t)12 * V;
   const int mi = a.prm->max_iter;
-  T* base = a.ring + (size_t)r * 3 * n12;
+  T* base = a.ring + (size_t)r * a.prm->nslots * n12;
   const T* Ui = base + (size_t)(i % 3) * n12;
   const T* Um = base + (size_t)((i + 2) % 3) * n12;
   T* W = base + (size_t)((i + 1) % 3) * n12;
@@ -473,7 +483,7 @@ __global__ void __launch_bounds__(NT2) lanczos_init_kernel(SolveArgs<R> a, const
   __shared__ bool last;
   const int r = blockIdx.y;
   const size_t n12 = (size_t)12 * a.g.V;
-  T* U1 = a.ring + (size_t)r * 3 * n12 + n12;
+  T* U1 = a.ring + (size_t)r * a.prm->nslots * n12 + n12;
   const size_t e = (size_t)blockIdx.x * NT2 + threadIdx.x;
   double nrm = 0.0;
   if (e < n12) {
@@ -516,18 +526,21 @@ __global__ void __launch_bounds__(NT2) lanczos_init_kernel(SolveArgs<R> a, const
     q.active = 1;
     q.last_iter = 0;
   }
-  if (!(S->bnorm > 0.0) || !isfinite(S->bnorm)) {
+  // a source whose tolerance is >= 1 needs no work (a correction right-hand side that
+  // already meets tol): done before the first step, which could otherwise enlarge it
+  const bool skip = a.tol_src && a.tol_src[r] >= 1.0;
+  if (skip || !(S->bnorm > 0.0) || !isfinite(S->bnorm)) {
     for (int j = 0; j < ns; ++j) {
       a.sh[(size_t)r * ns + j].active = 0;
       a.sh[(size_t)r * ns + j].res = 0.0;
     }
-    mark_done(S, a.done_count, isfinite(S->bnorm) ? OV_OK : OV_ERR_BREAKDOWN);
+    mark_done(S, a.done_count, (skip || isfinite(S->bnorm)) ? OV_OK : OV_ERR_BREAKDOWN);
   }
 }
 
 // second pass: U_1 = b again in ring slot 1 (the first pass overwrote the ring)
 template <typename R>
-__global__ void ring_reset_kernel(SolveArgs<R> a, const double2* __restrict__ b, int nsrc) {
+__global__ void ring_reset_kernel(SolveArgs<R> a, const double2* __restrict__ b, int nsrc, int nslots) {
   using T = typename Store<R>::T;
   const size_t n12 = (size_t)12 * a.g.V;
   const size_t n = n12 * nsrc;
@@ -537,7 +550,7 @@ __global__ void ring_reset_kernel(SolveArgs<R> a, const double2* __restrict__ b,
     T v;
     v.x = bv.x;
     v.y = bv.y;
-    a.ring[r * 3 * n12 + n12 + e] = v;
+    a.ring[r * nslots * n12 + n12 + e] = v;
   }
 }
 
@@ -563,12 +576,13 @@ template <typename R>
 struct SolveWs {
   SolveArgs<R> a{};
   int nblk1 = 0, nblk2 = 0;
+  int nslots = 3;
   SolveParams* prm_dev = nullptr;
 };
 
 template <typename R>
 int setup_ws(ov_ctx* ctx, int nsrc, int ns, bool want_x, bool want_sacc, bool want_hist, int max_iter,
-             SolveWs<R>* w, const char* tag) {
+             SolveWs<R>* w, const char* tag, int nslots = 3) {
   using T = typename Store<R>::T;
   const int V = ctx->g.V;
   const size_t n12 = (size_t)12 * V;
@@ -577,7 +591,8 @@ int setup_ws(ov_ctx* ctx, int nsrc, int ns, bool want_x, bool want_sacc, bool wa
   w->nblk1 = (V + kSplitSites - 1) / kSplitSites;
   w->nblk2 = (int)((n12 + NT2 - 1) / NT2);
   auto& a = w->a;
-  a.ring = (T*)ws_get(ctx, (t + ".ring").c_str(), sizeof(T) * 3 * n12 * nsrc, &st);
+  w->nslots = nslots;
+  a.ring = (T*)ws_get(ctx, (t + ".ring").c_str(), sizeof(T) * (size_t)nslots * n12 * nsrc, &st);
   a.p = ns ? (T*)ws_get(ctx, (t + ".p").c_str(), sizeof(T) * n12 * (size_t)nsrc * ns, &st) : nullptr;
   a.x = (want_x && ns) ? (T*)ws_get(ctx, (t + ".x").c_str(), sizeof(T) * n12 * (size_t)nsrc * ns, &st) : nullptr;
   a.sacc = want_sacc ? (double2*)ws_get(ctx, (t + ".sacc").c_str(), sizeof(double2) * n12 * nsrc, &st) : nullptr;
@@ -601,6 +616,7 @@ int setup_ws(ov_ctx* ctx, int nsrc, int ns, bool want_x, bool want_sacc, bool wa
     a.hist_a = a.hist_b = nullptr;
   }
   a.gco = nullptr;
+  a.tol_src = nullptr;
   w->prm_dev = (SolveParams*)ws_get(ctx, (t + ".prm").c_str(), sizeof(SolveParams), &st);
   a.prm = w->prm_dev;
   a.stencil = nullptr;
@@ -682,7 +698,7 @@ template <typename R>
 int init_solve(ov_ctx* ctx, SolveWs<R>& w, const double2* b_soa, int nsrc, int ns,
                const std::vector<double2>& zh, const std::vector<double2>& ch, double2 c0,
                double tol, int max_iter, cudaStream_t s, int vec_shifts = 1) {
-  SolveParams prm{tol, max_iter, ns, vec_shifts};
+  SolveParams prm{tol, max_iter, ns, vec_shifts, w.nslots, w.nslots > 3 ? 1 : 0};
   cudaError_t e = cudaMemcpyAsync(w.prm_dev, &prm, sizeof(prm), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy params");
   if (ns > 0) {
@@ -855,7 +871,7 @@ int solve_sign_2pass(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int ns
   if (e == cudaSuccess) e = cudaMemsetAsync(w.a.cnt, 0, sizeof(unsigned) * 2 * nsrc, s);
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "second-pass setup");
   w.a.gco = gco;
-  ring_reset_kernel<double><<<256, 256, 0, s>>>(w.a, b_soa, nsrc);
+  ring_reset_kernel<double><<<256, 256, 0, s>>>(w.a, b_soa, nsrc, 3);
   launches += 1.0;
   // pass 2: kmax regeneration launches (no host reads), replayed from a graph
   const int chunk = o.check_every > 0 ? o.check_every : 32;
@@ -904,6 +920,191 @@ int solve_sign_2pass(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int ns
                       cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy sum");
   return fst;
+}
+
+// OV_MODE_MIXED.
+//  Phase A (FP32): one Lanczos process per source with FP32 vectors and FP64 scalars;
+//    every node's LDL^T recurrence runs on scalars (for the stopping test) and the basis
+//    is kept (slot i = U_i; GB300's HBM holds hundreds of basis vectors per source).  The
+//    host forms each node's FOM coefficients (z_j - T_k)^-1 e_1 ||b|| and a combination
+//    kernel writes y_j = sum_i w_ij U_i in FP64.
+//  Rounds: FP64 true residuals r_j = b - (z_j - H_W) y_j (FP64 stencil fused) for every
+//    node and source; if any exceeds tol ||b||, one batched FP32 correction solve over
+//    all nodes x sources (each right-hand side its own Lanczos process with its single
+//    shift z_j, per-RHS tolerance, converged ones leave the batch), y_j += e_j in FP64.
+//  Finally the FP64 weighted sum s = c0 b + sum_j c_j y_j.
+int solve_sign_mixed(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc, const ov_solve_opts& o,
+                     SolveOut* so, cudaStream_t s) {
+  const int nq = (int)ctx->z.size();
+  const size_t n12 = (size_t)12 * ctx->g.V;
+  const int nrhs = nsrc * nq;
+  int st = OV_OK;
+  cudaError_t e;
+  // basis capacity: at most 600 vectors per source, a third of device memory and max_iter
+  size_t freeb = 0, totalb = 0;
+  cudaMemGetInfo(&freeb, &totalb);
+  const size_t per_slot = (size_t)nsrc * n12 * sizeof(float2);
+  long long cap = (long long)(0.33 * (double)totalb / (double)per_slot) - 2;
+  const int kcap = (int)std::max<long long>(8, std::min<long long>(std::min<long long>(cap, 600), o.max_iter));
+  double launches = 0.0;
+
+  // ---- phase A
+  std::vector<double2> zh((size_t)nsrc * nq), ch((size_t)nsrc * nq);
+  for (int r = 0; r < nsrc; ++r)
+    for (int j = 0; j < nq; ++j) {
+      zh[(size_t)r * nq + j] = ctx->z[j];
+      ch[(size_t)r * nq + j] = ctx->c[j];
+    }
+  SolveWs<float> wA;
+  st = setup_ws<float>(ctx, nsrc, nq, false, false, true, kcap, &wA, "mxA", kcap + 2);
+  if (st != OV_OK) return st;
+  const double tolA = std::max(o.tol, 1e-6);
+  st = init_solve<float>(ctx, wA, b_soa, nsrc, nq, zh, ch, make_double2(0, 0), tolA, kcap, s, 0);
+  if (st != OV_OK) return st;
+  launches += 1;
+  st = run_iterations<float>(ctx, wA, nsrc, nq, 4, kcap, o, s, &launches);
+  if (st != OV_OK) return st;
+  SolveOut soA;
+  const int fa = finish_solve<float>(ctx, wA, nsrc, nq, zh, ch, &soA, s);
+  if (fa == OV_ERR_BREAKDOWN) return fa;
+  std::vector<SrcState> S(nsrc);
+  std::vector<double> ha((size_t)nsrc * kcap), hb((size_t)nsrc * kcap);
+  e = cudaMemcpyAsync(S.data(), wA.a.src, sizeof(SrcState) * nsrc, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ha.data(), wA.a.hist_a, sizeof(double) * ha.size(), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), wA.a.hist_b, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "read phase-A history");
+  int kmax = 1;
+  std::vector<int> kr(nsrc);
+  for (int r = 0; r < nsrc; ++r) {
+    kr[r] = std::max(0, S[r].iter - 1);
+    kmax = std::max(kmax, kr[r]);
+  }
+  // w_ij = [(z_j - T_k)^-1 e_1 ||b||]_i / ||U_i||  (the basis is stored unnormalised)
+  std::vector<float2> W((size_t)nsrc * nq * kmax, make_float2(0.f, 0.f));
+  std::vector<std::complex<double>> dd, ll, zt, yy;
+  for (int r = 0; r < nsrc; ++r) {
+    const int k = kr[r];
+    if (k < 1) continue;
+    const double* al = ha.data() + (size_t)r * kcap;
+    const double* be = hb.data() + (size_t)r * kcap;
+    dd.assign(k, 0.0);
+    ll.assign(k, 0.0);
+    zt.assign(k, 0.0);
+    yy.assign(k, 0.0);
+    for (int j = 0; j < nq; ++j) {
+      const std::complex<double> zj(ctx->z[j].x, ctx->z[j].y);
+      std::complex<double> om = S[r].bnorm;
+      for (int i = 0; i < k; ++i) {
+        if (i == 0) {
+          dd[0] = zj - al[0];
+        } else {
+          dd[i] = zj - al[i] - be[i - 1] * be[i - 1] / dd[i - 1];
+          om = -ll[i - 1] * om;
+        }
+        ll[i] = -be[i] / dd[i];
+        zt[i] = om / dd[i];
+      }
+      yy[k - 1] = zt[k - 1];
+      for (int i = k - 2; i >= 0; --i) yy[i] = zt[i] - ll[i] * yy[i + 1];
+      for (int i = 0; i < k; ++i) {
+        const double ni = (i == 0) ? S[r].bnorm : be[i - 1];
+        const std::complex<double> w = yy[i] / ni;
+        W[((size_t)r * nq + j) * kmax + i] = make_float2((float)w.real(), (float)w.imag());
+      }
+    }
+  }
+  float2* Wd = (float2*)ws_get(ctx, "mx.W", sizeof(float2) * W.size(), &st);
+  int* krd = (int*)ws_get(ctx, "mx.kr", sizeof(int) * nsrc, &st);
+  double2* Y = (double2*)ws_get(ctx, "mx.Y", sizeof(double2) * n12 * nrhs, &st);
+  double2* R = (double2*)ws_get(ctx, "mx.R", sizeof(double2) * n12 * nrhs, &st);
+  double* part = (double*)ws_get(ctx, "mx.part", sizeof(double) * (size_t)residual64_partials(ctx) * nrhs, &st);
+  double* rn2 = (double*)ws_get(ctx, "mx.rn2", sizeof(double) * nrhs, &st);
+  double2* zd = (double2*)ws_get(ctx, "mx.z", sizeof(double2) * nq, &st);
+  double2* cd = (double2*)ws_get(ctx, "mx.c", sizeof(double2) * nq, &st);
+  double* told = (double*)ws_get(ctx, "mx.tol", sizeof(double) * nrhs, &st);
+  if (st != OV_OK) return st;
+  e = cudaMemcpyAsync(Wd, W.data(), sizeof(float2) * W.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(krd, kr.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(zd, ctx->z.data(), sizeof(double2) * nq, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cd, ctx->c.data(), sizeof(double2) * nq, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "phase-A coefficients");
+  st = launch_basis_combine(ctx, wA.a.ring, kcap + 2, Wd, kmax, krd, Y, nsrc, nq, s);
+  if (st != OV_OK) return st;
+  launches += 1;
+
+  // ---- FP64 residuals and FP32 corrections
+  std::vector<double> rn(nrhs), tol_h(nrhs);
+  const int max_rounds = 4;
+  so->refine_rounds = 0;
+  so->inner_iterations = 0;
+  so->node_updates = soA.node_updates;
+  double maxres = 0.0, bound = 0.0;
+  std::string hist;
+  for (int round = 0;; ++round) {
+    st = launch_residual64(ctx, Y, b_soa, zd, R, part, rn2, nsrc, nq, s);
+    if (st != OV_OK) return st;
+    launches += 2;
+    e = cudaMemcpyAsync(rn.data(), rn2, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "read residual norms");
+    maxres = 0.0;
+    bound = 0.0;
+    bool bad = false;
+    for (int r = 0; r < nsrc; ++r) {
+      const double bn = S[r].bnorm > 0 ? S[r].bnorm : 1.0;
+      double bd = 0.0;
+      for (int j = 0; j < nq; ++j) {
+        const double res = std::sqrt(rn[(size_t)r * nq + j]) / bn;
+        if (!std::isfinite(res)) bad = true;
+        maxres = std::max(maxres, res);
+        bd += std::hypot(ctx->c[j].x, ctx->c[j].y) * res / std::fabs(ctx->z[j].y);
+        // FP32 corrections reach ~1e-6 relative: ask for that, or what tol needs
+        tol_h[(size_t)r * nq + j] = res <= o.tol ? 1e30 : std::max(0.3 * o.tol / res, 2e-6);
+      }
+      bound = std::max(bound, bd);
+    }
+    if (bad) return ctx_fail(ctx, OV_ERR_BREAKDOWN, "non-finite residual in the mixed-precision solve");
+    char buf[64];
+    snprintf(buf, sizeof buf, "%s%.3g", round ? ", " : "", maxres);
+    hist += buf;
+    if (maxres <= o.tol || round >= max_rounds) break;
+    ++so->refine_rounds;
+    std::vector<double2> zc(nrhs), cc(nrhs, make_double2(1.0, 0.0));
+    for (int r = 0; r < nsrc; ++r)
+      for (int j = 0; j < nq; ++j) zc[(size_t)r * nq + j] = ctx->z[j];
+    SolveWs<float> wC;
+    st = setup_ws<float>(ctx, nrhs, 1, true, false, false, o.max_iter, &wC, "mxC");
+    if (st != OV_OK) return st;
+    e = cudaMemcpyAsync(told, tol_h.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy tolerances");
+    wC.a.tol_src = told;
+    st = init_solve<float>(ctx, wC, R, nrhs, 1, zc, cc, make_double2(0, 0), 0.5, o.max_iter, s, 1);
+    if (st != OV_OK) return st;
+    launches += 2;
+    st = run_iterations<float>(ctx, wC, nrhs, 1, 5, o.max_iter, o, s, &launches);
+    if (st != OV_OK) return st;
+    SolveOut soC;
+    const int fc = finish_solve<float>(ctx, wC, nrhs, 1, zc, cc, &soC, s);
+    if (fc == OV_ERR_BREAKDOWN) return fc;
+    so->inner_iterations += soC.iterations;
+    so->node_updates += soC.node_updates;
+    st = launch_accumulate(ctx, Y, wC.a.x, n12 * nrhs, s);
+    if (st != OV_OK) return st;
+    launches += 1;
+  }
+  st = launch_weighted_sum(ctx, Y, b_soa, cd, ctx->c0, out_soa, nsrc, nq, s);
+  if (st != OV_OK) return st;
+  so->iterations = soA.iterations;
+  so->max_residual = maxres;
+  so->error_bound = bound;
+  so->converged = maxres <= o.tol;
+  so->launches = launches + 3;
+  if (!so->converged)
+    return ctx_fail(ctx, OV_ERR_NOT_CONVERGED,
+                    "mixed-precision refinement did not reach tol; max relative FP64 residual after phase A and "
+                    "each correction round: " + hist);
+  return OV_OK;
 }
 
 // Lanczos tridiagonal of H_W (squared = 0) or H_W^2 (squared = 1) from a fixed
