@@ -94,6 +94,9 @@ typedef struct {
                        from the device are enqueued on `stream` inside the call  [0] */
   int check_every;  /* iterations between host reads of the convergence flag  [32] */
   int use_graph;    /* 1: replay the per-iteration kernels from a CUDA graph     [1] */
+  int node_chunk;   /* VJP: nodes whose forward and adjoint solutions are held at once;
+                       0 = all.  Smaller values recompute the Krylov solve per chunk of
+                       nodes: memory 2 x node_chunk x 12V complex doubles, work x chunks [0] */
 } ov_solve_opts;
 
 /* Per-call statistics (optional output, may be NULL). */
@@ -171,7 +174,7 @@ int ov_sgn_HW_apply(ov_ctx* ctx, const void* b, void* out, int nrhs, const ov_so
 int ov_overlap_apply(ov_ctx* ctx, double m_q, const void* b, void* out, int nrhs,
                      const ov_solve_opts* opts, ov_stats* stats, void* stream);
 
-/* Gradients of L = Re <eta, S_N b> (one source):
+/* Gradients of L = Re <eta, S_N b> (one source; FP64 shifted solves whatever opts->mode):
  *   grad_b     = S_N^dag eta (complex double spinor): dL = Re <grad_b, db>;
  *   grad_links = dL/d omega_{x,mu,a} for U_mu(x) -> exp(i omega_a lambda_a/2) U_mu(x)
  *                (double [mu][t][z][y][x][8]).

@@ -122,6 +122,7 @@ ov_solve_opts resolve_opts(const ov_solve_opts* o) {
   r.host_io = 0;
   r.check_every = 32;
   r.use_graph = 1;
+  r.node_chunk = 0;
   if (o) r = *o;
   if (r.check_every <= 0) r.check_every = 32;
   return r;
@@ -515,16 +516,135 @@ int ov_overlap_apply(ov_ctx* ctx, double m_q, const void* b, void* out, int nrhs
   return sign_or_overlap(ctx, true, m_q, b, out, nrhs, opts, stats, stream);
 }
 
+}  // extern "C"
+
+namespace {
+
+__global__ void axpy_c_kernel(double2* __restrict__ y, const double2* __restrict__ x, double2 c, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = x[t];
+    double2 w = y[t];
+    w.x += c.x * v.x - c.y * v.y;
+    w.y += c.x * v.y + c.y * v.x;
+    y[t] = w;
+  }
+}
+
+__global__ void scale_kernel(double* __restrict__ p, double a, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    p[t] *= a;
+}
+
+// Shared core of the two VJP entry points.  eta_s is the adjoint source of the sign
+// function (eta, or gamma5 eta for the overlap operator); grad_b = a eta + gsc S_N^dag eta_s;
+// force = fsc * dRe<eta_s, S_N b>/d omega.
+int vjp_core(ov_ctx* ctx, double a_eta, double gsc, double fsc, bool gamma5_eta, const void* eta, const void* b,
+             void* grad_b, double* grad_links, const ov_solve_opts* opts, ov_stats* stats, void* stream) {
+  const double t0 = now_ms();
+  if (!ctx) return OV_ERR_INVALID_ARG;
+  if (!ctx->have_gauge) return ctx_fail(ctx, OV_ERR_NO_GAUGE, "ov_set_gauge has not been called");
+  if (!ctx->have_contour) return ctx_fail(ctx, OV_ERR_NO_CONTOUR, "no contour set");
+  if (!eta || !b) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "null eta or b");
+  ov_solve_opts o = resolve_opts(opts);
+  int st = check_opts(ctx, o);
+  if (st != OV_OK) return st;
+  if (!grad_b && !grad_links) return OV_OK;
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int V = ctx->g.V;
+  const size_t n12 = (size_t)12 * V;
+  const int nq = (int)ctx->z.size();
+  const int chunk = (o.node_chunk > 0 && o.node_chunk < nq) ? o.node_chunk : nq;
+  const double2* etad = stage_in(ctx, eta, sizeof(double2) * n12, o.host_io, "vjp.eta", s, &st);
+  const double2* bd = stage_in(ctx, b, sizeof(double2) * n12, o.host_io, "vjp.b", s, &st);
+  double2* src2 = (double2*)ws_get(ctx, "vjp.src", sizeof(double2) * 2 * n12, &st);  // [b; eta_s] SoA
+  double2* gb = (double2*)ws_get(ctx, "vjp.gb", sizeof(double2) * n12, &st);
+  double2* gbo = (double2*)ws_get(ctx, "vjp.gbo", sizeof(double2) * n12, &st);
+  double2* sums = (double2*)ws_get(ctx, "vjp.sums", sizeof(double2) * 2 * n12, &st);
+  double2* X = (double2*)ws_get(ctx, "vjp.X", sizeof(double2) * 2 * n12 * chunk, &st);
+  double* F = (double*)ws_get(ctx, "vjp.F", sizeof(double) * 4 * 8 * (size_t)V, &st);
+  double2* cq = (double2*)ws_get(ctx, "vjp.c", sizeof(double2) * chunk, &st);
+  double2* etag = (double2*)ws_get(ctx, "vjp.eta5", sizeof(double2) * n12, &st);
+  if (st != OV_OK) return st;
+  // sources in structure of arrays: b, and eta (or gamma5 eta)
+  if ((st = launch_pack64(ctx, bd, src2, 1, s))) return st;
+  const double2* es = etad;
+  if (gamma5_eta) {
+    if ((st = launch_gamma5_aos(ctx, etad, etag, 1, s))) return st;
+    es = etag;
+  }
+  if ((st = launch_pack64(ctx, es, src2 + n12, 1, s))) return st;
+  // grad_b starts as a_eta * eta (SoA) + gsc * conj(c0) eta_s
+  double2* eta_soa = gb;  // reuse: pack eta into gb then scale
+  if ((st = launch_pack64(ctx, etad, eta_soa, 1, s))) return st;
+  scale_kernel<<<512, 256, 0, s>>>((double*)gb, a_eta, 2 * n12);
+  axpy_c_kernel<<<512, 256, 0, s>>>(gb, src2 + n12, make_double2(gsc * ctx->c0.x, -gsc * ctx->c0.y), n12);
+  cudaMemsetAsync(F, 0, sizeof(double) * 32 * (size_t)V, s);
+  SolveOut tot;
+  tot.converged = 1;
+  for (int j0 = 0; j0 < nq; j0 += chunk) {
+    const int nc = std::min(chunk, nq - j0);
+    // source 0 (b): nodes z_j; source 1 (eta_s): nodes conj(z_j), coefficients conj(c_j)
+    std::vector<double2> zh(2 * (size_t)nc), ch(2 * (size_t)nc), cj(nc);
+    for (int j = 0; j < nc; ++j) {
+      const double2 z = ctx->z[j0 + j], c = ctx->c[j0 + j];
+      zh[j] = z;
+      ch[j] = c;
+      zh[nc + j] = make_double2(z.x, -z.y);
+      ch[nc + j] = make_double2(c.x, -c.y);
+      cj[j] = c;
+    }
+    SolveOut so;
+    st = solve_nodes_soa(ctx, src2, 2, nc, zh, ch, make_double2(0, 0), sums, X, o, &so, s);
+    if (st != OV_OK && st != OV_ERR_NOT_CONVERGED) return st;
+    if (st == OV_ERR_NOT_CONVERGED) tot.converged = 0;
+    tot.iterations += so.iterations;
+    tot.max_residual = std::max(tot.max_residual, so.max_residual);
+    tot.error_bound += so.error_bound;
+    tot.node_updates += so.node_updates;
+    tot.launches += so.launches;
+    // grad_b += gsc * sum_j conj(c_j) xi_j (the second source's weighted sum)
+    axpy_c_kernel<<<512, 256, 0, s>>>(gb, sums + n12, make_double2(gsc, 0.0), n12);
+    if (grad_links) {
+      cudaError_t e = cudaMemcpyAsync(cq, cj.data(), sizeof(double2) * nc, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy coefficients");
+      if ((st = launch_force(ctx, X, nc, cq, F, s))) return st;
+    }
+  }
+  if (fsc != 1.0) scale_kernel<<<512, 256, 0, s>>>(F, fsc, 32 * (size_t)V);
+  OV_CHECK_LAUNCH(ctx, "vjp kernels");
+  cudaError_t e = cudaSuccess;
+  if (grad_b) {
+    double2* dst = o.host_io ? gbo : (double2*)grad_b;
+    if ((st = launch_unpack64(ctx, gb, dst, 1, s))) return st;
+    if (o.host_io) e = cudaMemcpyAsync(grad_b, gbo, sizeof(double2) * n12, cudaMemcpyDeviceToHost, s);
+  }
+  if (e == cudaSuccess && grad_links)
+    e = cudaMemcpyAsync(grad_links, F, sizeof(double) * 32 * (size_t)V,
+                        o.host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "VJP outputs");
+  kt_collect(ctx);
+  fill_stats(stats, tot, now_ms() - t0);
+  if (!tot.converged) return ctx_fail(ctx, OV_ERR_NOT_CONVERGED, "VJP solves hit the iteration limit");
+  return OV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int ov_sgn_vjp(ov_ctx* ctx, const void* eta, const void* b, void* grad_b, double* grad_links,
                const ov_solve_opts* opts, ov_stats* stats, void* stream) {
-  (void)eta; (void)b; (void)grad_b; (void)grad_links; (void)opts; (void)stats; (void)stream;
-  return ctx_fail(ctx, OV_ERR_INVALID_ARG, "ov_sgn_vjp is not available in this build");
+  return vjp_core(ctx, 0.0, 1.0, 1.0, false, eta, b, grad_b, grad_links, opts, stats, stream);
 }
 
 int ov_overlap_vjp(ov_ctx* ctx, double m_q, const void* eta, const void* b, void* grad_b, double* grad_links,
                    const ov_solve_opts* opts, ov_stats* stats, void* stream) {
-  (void)m_q; (void)eta; (void)b; (void)grad_b; (void)grad_links; (void)opts; (void)stats; (void)stream;
-  return ctx_fail(ctx, OV_ERR_INVALID_ARG, "ov_overlap_vjp is not available in this build");
+  if (!std::isfinite(m_q)) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "m_q is not finite");
+  // L = Re<eta, (1+m)/2 b> + (1-m)/2 Re<gamma5 eta, S_N b>
+  return vjp_core(ctx, 0.5 * (1.0 + m_q), 0.5 * (1.0 - m_q), 0.5 * (1.0 - m_q), true, eta, b, grad_b, grad_links,
+                  opts, stats, stream);
 }
 
 int ov_set_hw32_variant(ov_ctx* ctx, int k) {

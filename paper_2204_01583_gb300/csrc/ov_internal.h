@@ -164,6 +164,10 @@ int solve_sign_soa(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nrhs
                    const ov_solve_opts& o, SolveOut* so, cudaStream_t s,
                    double2* xs_soa /* optional per-node solutions [src][node][12V] */);
 
+int solve_nodes_soa(ov_ctx* ctx, const double2* b_soa, int nsrc, int ns, const std::vector<double2>& zh,
+                    const std::vector<double2>& ch, double2 c0, double2* out_soa, double2* xs_soa,
+                    const ov_solve_opts& o, SolveOut* so, cudaStream_t s);
+
 // two-pass FP64 variant (OV_MODE_FP64_2PASS)
 int solve_sign_2pass(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nrhs, const ov_solve_opts& o,
                      SolveOut* so, cudaStream_t s);
@@ -184,9 +188,8 @@ int launch_weighted_sum(ov_ctx* ctx, const double2* Y, const double2* b, const d
 int lanczos_tridiag(ov_ctx* ctx, int steps, int squared, std::vector<double>& alpha,
                     std::vector<double>& beta, cudaStream_t s);
 
-// force (force.cu): F[mu][site][8] += ... from per-node y and xi (SoA)
-int launch_force(ov_ctx* ctx, const double2* y, const double2* xi, int nnode, const double2* coef,
-                 double* F_aos, cudaStream_t s);
+// force (force.cu): F[mu][site][8] += force from X = [forward y_j (nq); adjoint xi_j (nq)] (SoA)
+int launch_force(ov_ctx* ctx, const double2* X, int nq, const double2* cq, double* F, cudaStream_t s);
 
 // host-side contour math (contour.cpp)
 void ellipse_rule(int n_q, double gamma, double rho, double alpha, int form, std::vector<double2>& z,

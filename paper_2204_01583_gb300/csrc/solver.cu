@@ -762,31 +762,42 @@ int finish_solve(ov_ctx* ctx, SolveWs<R>& w, int nsrc, int ns, const std::vector
 
 }  // namespace
 
-int solve_sign_soa(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc, const ov_solve_opts& o,
-                   SolveOut* so, cudaStream_t s, double2* xs_soa) {
-  const int ns = (int)ctx->z.size();
+// Shifted FP64 solve with an explicit node list per source (zh, ch: nsrc x ns): the
+// weighted sum c0 b + sum_j c_j y_j goes to out_soa (if not null) and, if xs_soa is
+// not null, every node's solution y_j to xs_soa[src][j][12V].
+int solve_nodes_soa(ov_ctx* ctx, const double2* b_soa, int nsrc, int ns, const std::vector<double2>& zh,
+                    const std::vector<double2>& ch, double2 c0, double2* out_soa, double2* xs_soa,
+                    const ov_solve_opts& o, SolveOut* so, cudaStream_t s) {
   SolveWs<double> w;
   int st = setup_ws<double>(ctx, nsrc, ns, xs_soa != nullptr, true, false, o.max_iter, &w, "fp64");
   if (st != OV_OK) return st;
   if (xs_soa) w.a.x = xs_soa;
-  std::vector<double2> zh((size_t)nsrc * ns), ch((size_t)nsrc * ns);
-  for (int r = 0; r < nsrc; ++r)
-    for (int j = 0; j < ns; ++j) {
-      zh[(size_t)r * ns + j] = ctx->z[j];
-      ch[(size_t)r * ns + j] = ctx->c[j];
-    }
-  st = init_solve<double>(ctx, w, b_soa, nsrc, ns, zh, ch, ctx->c0, o.tol, o.max_iter, s);
+  st = init_solve<double>(ctx, w, b_soa, nsrc, ns, zh, ch, c0, o.tol, o.max_iter, s);
   if (st != OV_OK) return st;
   double launches = 1.0 + (xs_soa ? 1.0 : 0.0);  // init (+ zeroing)
   st = run_iterations<double>(ctx, w, nsrc, ns, xs_soa ? 1 : 0, o.max_iter, o, s, &launches);
   if (st != OV_OK) return st;
   st = finish_solve<double>(ctx, w, nsrc, ns, zh, ch, so, s);
   so->launches = launches + 2.0;  // pack + unpack/epilogue issued by the caller
-  // copy the weighted sum out even when not converged (best iterate)
-  cudaError_t e = cudaMemcpyAsync(out_soa, w.a.sacc, sizeof(double2) * 12 * (size_t)ctx->g.V * nsrc,
-                                  cudaMemcpyDeviceToDevice, s);
-  if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy sum");
+  if (out_soa) {
+    // the weighted sum, even when not converged (best iterate)
+    cudaError_t e = cudaMemcpyAsync(out_soa, w.a.sacc, sizeof(double2) * 12 * (size_t)ctx->g.V * nsrc,
+                                    cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy sum");
+  }
   return st;
+}
+
+int solve_sign_soa(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc, const ov_solve_opts& o,
+                   SolveOut* so, cudaStream_t s, double2* xs_soa) {
+  const int ns = (int)ctx->z.size();
+  std::vector<double2> zh((size_t)nsrc * ns), ch((size_t)nsrc * ns);
+  for (int r = 0; r < nsrc; ++r)
+    for (int j = 0; j < ns; ++j) {
+      zh[(size_t)r * ns + j] = ctx->z[j];
+      ch[(size_t)r * ns + j] = ctx->c[j];
+    }
+  return solve_nodes_soa(ctx, b_soa, nsrc, ns, zh, ch, ctx->c0, out_soa, xs_soa, o, so, s);
 }
 
 // OV_MODE_FP64_2PASS.  Pass 1: the Lanczos process with every node's LDL^T scalar

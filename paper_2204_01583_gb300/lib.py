@@ -41,7 +41,8 @@ EXPORTS = (
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("host_io", ctypes.c_int), ("check_every", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("host_io", ctypes.c_int), ("check_every", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("node_chunk", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -200,9 +201,9 @@ class Context:
                                      _stream_ptr(stream)))
 
     @staticmethod
-    def opts(mode="fp64", tol=1e-12, max_iter=20000, host_io=False, check_every=32, use_graph=True):
+    def opts(mode="fp64", tol=1e-12, max_iter=20000, host_io=False, check_every=32, use_graph=True, node_chunk=0):
         return SolveOpts(MODES[mode] if isinstance(mode, str) else int(mode), float(tol), int(max_iter),
-                         int(bool(host_io)), int(check_every), int(bool(use_graph)))
+                         int(bool(host_io)), int(check_every), int(bool(use_graph)), int(node_chunk))
 
     def sgn(self, b, out, nrhs, opts=None, stream=None, allow_not_converged=False):
         st = Stats()
