@@ -73,11 +73,16 @@ typedef enum {
    * residuals and FP32 defect-correction solves over all nodes x sources in
    * one multi-RHS launch, FP64 quadrature sum. */
   OV_MODE_MIXED = 1,
-  /* FP64 two-pass Lanczos: the per-node recurrences of OV_MODE_FP64 are carried
-   * out on the tridiagonal Lanczos matrix instead of on vectors; a second
-   * Lanczos pass rebuilds the basis and accumulates the sum.  Same result,
-   * vector work independent of the number of nodes. */
-  OV_MODE_FP64_2PASS = 2
+  /* FP64 coefficient-space Lanczos: the per-node recurrences of OV_MODE_FP64 are
+   * carried out on the tridiagonal Lanczos matrix instead of on vectors, and the sum
+   * of Eq. 7 becomes sum_i g_i v_i over the Lanczos basis.  The basis is kept in device
+   * memory when min(max_iter, 1024) vectors per source fit a quarter of it (the sum is
+   * then one read of the basis); otherwise a second Lanczos pass regenerates it.
+   * Same result as OV_MODE_FP64 up to rounding; vector work independent of N. */
+  OV_MODE_FP64_2PASS = 2,
+  /* As OV_MODE_FP64_2PASS, always regenerating the basis (memory: three vectors per
+   * source). */
+  OV_MODE_FP64_REGEN = 3
 } ov_mode;
 
 typedef enum {

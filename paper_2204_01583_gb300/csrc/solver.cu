@@ -474,6 +474,29 @@ __global__ void __launch_bounds__(NT1) lanczos_regen_kernel(SolveArgs<R> a) {
   }
 }
 
+// Stored-basis variant of the second pass: sum[r][e] += sum_{i=1..k_r} gw[r][i-1] U_i[e],
+// gw = g_i / ||U_i|| (the basis is stored unnormalised).  Reads the basis once.
+__global__ void basis_sum_kernel(const double2* __restrict__ basis, int nslots, const double2* __restrict__ gw,
+                                 int ldg, const int* __restrict__ kr, double2* __restrict__ sum, size_t n12) {
+  const int r = blockIdx.y;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n12) return;
+  const double2* B = basis + (size_t)r * nslots * n12 + e;
+  const double2* w = gw + (size_t)r * ldg;
+  double re = 0.0, im = 0.0;
+  const int k = kr[r];
+  for (int i = 1; i <= k; ++i) {
+    const double2 u = __ldg(B + (size_t)i * n12);
+    const double2 c = __ldg(w + i - 1);
+    re = fma(c.x, u.x, fma(-c.y, u.y, re));
+    im = fma(c.x, u.y, fma(c.y, u.x, im));
+  }
+  double2 sv = sum[(size_t)r * n12 + e];
+  sv.x += re;
+  sv.y += im;
+  sum[(size_t)r * n12 + e] = sv;
+}
+
 // Init: U_1 = b (ring slot 1), ||b|| per source, s = c0 b, node states reset.
 template <typename R>
 __global__ void __launch_bounds__(NT2) lanczos_init_kernel(SolveArgs<R> a, const double2* __restrict__ b,
@@ -800,6 +823,110 @@ int solve_sign_soa(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc
   return solve_nodes_soa(ctx, b_soa, nsrc, ns, zh, ch, ctx->c0, out_soa, xs_soa, o, so, s);
 }
 
+// g = sum_j c_j (z_j - T_k)^-1 e_1 ||b|| per source (forward LDL^T sweep and back
+// substitution per node), from the recorded alpha (ha) and beta (hb), leading dimension ld.
+static void lanczos_sum_coefficients(const ov_ctx* ctx, int nsrc, const std::vector<int>& kr,
+                                     const std::vector<double>& bnorm, const std::vector<double>& ha,
+                                     const std::vector<double>& hb, int ld, std::vector<double2>& g) {
+  const int ns = (int)ctx->z.size();
+  g.assign((size_t)nsrc * ld, make_double2(0.0, 0.0));
+  std::vector<std::complex<double>> dd, ll, zt, yy;
+  for (int r = 0; r < nsrc; ++r) {
+    const int k = kr[r];
+    if (k < 1) continue;
+    const double* al = ha.data() + (size_t)r * ld;
+    const double* be = hb.data() + (size_t)r * ld;
+    dd.assign(k, 0.0);
+    ll.assign(k, 0.0);
+    zt.assign(k, 0.0);
+    yy.assign(k, 0.0);
+    for (int j = 0; j < ns; ++j) {
+      const std::complex<double> zj(ctx->z[j].x, ctx->z[j].y), cj(ctx->c[j].x, ctx->c[j].y);
+      std::complex<double> om = bnorm[r];
+      for (int i = 0; i < k; ++i) {
+        if (i == 0) {
+          dd[0] = zj - al[0];
+        } else {
+          dd[i] = zj - al[i] - be[i - 1] * be[i - 1] / dd[i - 1];
+          om = -ll[i - 1] * om;
+        }
+        ll[i] = -be[i] / dd[i];
+        zt[i] = om / dd[i];
+      }
+      yy[k - 1] = zt[k - 1];
+      for (int i = k - 2; i >= 0; --i) yy[i] = zt[i] - ll[i] * yy[i + 1];
+      for (int i = 0; i < k; ++i) {
+        const std::complex<double> t = cj * yy[i];
+        g[(size_t)r * ld + i].x += t.real();
+        g[(size_t)r * ld + i].y += t.imag();
+      }
+    }
+  }
+}
+
+// Stored-basis form of OV_MODE_FP64_2PASS: pass 1 keeps U_1 .. U_k (slot i), then
+// s = c0 b + sum_i (g_i / ||U_i||) U_i in one read of the basis.
+static int solve_sign_stored(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc,
+                             const ov_solve_opts& o, SolveOut* so, cudaStream_t s, int cap) {
+  const int ns = (int)ctx->z.size();
+  const size_t n12 = (size_t)12 * ctx->g.V;
+  SolveWs<double> w;
+  int st = setup_ws<double>(ctx, nsrc, ns, false, true, true, cap, &w, "fp64s", cap + 2);
+  if (st != OV_OK) return st;
+  std::vector<double2> zh((size_t)nsrc * ns), ch((size_t)nsrc * ns);
+  for (int r = 0; r < nsrc; ++r)
+    for (int j = 0; j < ns; ++j) {
+      zh[(size_t)r * ns + j] = ctx->z[j];
+      ch[(size_t)r * ns + j] = ctx->c[j];
+    }
+  st = init_solve<double>(ctx, w, b_soa, nsrc, ns, zh, ch, ctx->c0, o.tol, cap, s, 0);
+  if (st != OV_OK) return st;
+  double launches = 1.0;
+  st = run_iterations<double>(ctx, w, nsrc, ns, 6, cap, o, s, &launches);
+  if (st != OV_OK) return st;
+  const int fst = finish_solve<double>(ctx, w, nsrc, ns, zh, ch, so, s);
+  // not converged within the store: the caller regenerates, unless the store already
+  // spans max_iter (then the best iterate is returned with OV_ERR_NOT_CONVERGED)
+  if (fst != OV_OK && !(fst == OV_ERR_NOT_CONVERGED && cap >= o.max_iter)) return fst;
+  std::vector<SrcState> S(nsrc);
+  std::vector<double> ha((size_t)nsrc * cap), hb((size_t)nsrc * cap);
+  cudaError_t e = cudaMemcpyAsync(S.data(), w.a.src, sizeof(SrcState) * nsrc, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ha.data(), w.a.hist_a, sizeof(double) * ha.size(), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), w.a.hist_b, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "read Lanczos history");
+  std::vector<int> kr(nsrc);
+  std::vector<double> bn(nsrc);
+  for (int r = 0; r < nsrc; ++r) {
+    kr[r] = std::max(0, S[r].iter - 1);
+    bn[r] = S[r].bnorm;
+  }
+  std::vector<double2> g;
+  lanczos_sum_coefficients(ctx, nsrc, kr, bn, ha, hb, cap, g);
+  for (int r = 0; r < nsrc; ++r)
+    for (int i = 0; i < kr[r]; ++i) {  // fold in 1 / ||U_i||
+      const double ni = (i == 0) ? bn[r] : hb[(size_t)r * cap + i - 1];
+      g[(size_t)r * cap + i].x /= ni;
+      g[(size_t)r * cap + i].y /= ni;
+    }
+  double2* gd = (double2*)ws_get(ctx, "fp64s.g", sizeof(double2) * g.size(), &st);
+  int* krd = (int*)ws_get(ctx, "fp64s.kr", sizeof(int) * nsrc, &st);
+  if (st != OV_OK) return st;
+  e = cudaMemcpyAsync(gd, g.data(), sizeof(double2) * g.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(krd, kr.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy coefficients");
+  cudaEvent_t ev;
+  kt_begin(ctx, KC_REGEN, s, &ev);
+  basis_sum_kernel<<<dim3((unsigned)((n12 + 255) / 256), nsrc), 256, 0, s>>>(w.a.ring, cap + 2, gd, cap, krd,
+                                                                             w.a.sacc, n12);
+  kt_end(ctx, KC_REGEN, s, ev);
+  OV_CHECK_LAUNCH(ctx, "basis_sum_kernel");
+  so->launches = launches + 3.0;
+  e = cudaMemcpyAsync(out_soa, w.a.sacc, sizeof(double2) * n12 * nsrc, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy sum");
+  return fst;
+}
+
 // OV_MODE_FP64_2PASS.  Pass 1: the Lanczos process with every node's LDL^T scalar
 // recurrence (for the stopping test) but no per-node vectors; alpha_i and beta_i
 // are recorded.  Host: for every node the FOM coefficients y^j = (z_j - T_k)^-1 e_1 ||b||
@@ -810,6 +937,17 @@ int solve_sign_soa(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc
 int solve_sign_2pass(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc, const ov_solve_opts& o,
                      SolveOut* so, cudaStream_t s) {
   const int ns = (int)ctx->z.size();
+  // Keep the whole basis in HBM when up to min(max_iter, 1024) vectors per source fit a
+  // quarter of the device: then pass 2 is one read of the basis instead of a second
+  // Lanczos pass.  Otherwise (or if the solve outgrows the store) regenerate.
+  size_t freeb = 0, totalb = 0;
+  cudaMemGetInfo(&freeb, &totalb);
+  const int cap = std::min(o.max_iter, 1024);
+  const double store_bytes = (double)(cap + 2) * nsrc * 12.0 * ctx->g.V * sizeof(double2);
+  if (o.mode == OV_MODE_FP64_2PASS && store_bytes <= 0.25 * (double)totalb) {
+    const int st = solve_sign_stored(ctx, b_soa, out_soa, nsrc, o, so, s, cap);
+    if (st != OV_ERR_NOT_CONVERGED || cap >= o.max_iter) return st;
+  }
   SolveWs<double> w;
   int st = setup_ws<double>(ctx, nsrc, ns, false, true, true, o.max_iter, &w, "fp64");
   if (st != OV_OK) return st;
@@ -839,44 +977,21 @@ int solve_sign_2pass(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int ns
     e = cudaMemcpyAsync(hb.data(), w.a.hist_b, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "read Lanczos history");
-  std::vector<double2> g((size_t)nsrc * o.max_iter, make_double2(0.0, 0.0));
   int kmax = 0;
-  std::vector<std::complex<double>> dd, ll, zt, yy;
+  std::vector<int> kr(nsrc);
+  std::vector<double> bn(nsrc);
   for (int r = 0; r < nsrc; ++r) {
-    const int k = S[r].iter - 1;
-    S[r].k_final = k;
-    kmax = std::max(kmax, k);
-    if (k < 1) continue;
-    const double* al = ha.data() + (size_t)r * o.max_iter;
-    const double* be = hb.data() + (size_t)r * o.max_iter;
-    dd.assign(k, 0.0);
-    ll.assign(k, 0.0);
-    zt.assign(k, 0.0);
-    yy.assign(k, 0.0);
-    for (int j = 0; j < ns; ++j) {
-      const std::complex<double> zj(ctx->z[j].x, ctx->z[j].y), cj(ctx->c[j].x, ctx->c[j].y);
-      std::complex<double> om = S[r].bnorm;
-      for (int i = 0; i < k; ++i) {
-        if (i == 0) {
-          dd[0] = zj - al[0];
-        } else {
-          dd[i] = zj - al[i] - be[i - 1] * be[i - 1] / dd[i - 1];
-          om = -ll[i - 1] * om;
-        }
-        ll[i] = -be[i] / dd[i];
-        zt[i] = om / dd[i];
-      }
-      yy[k - 1] = zt[k - 1];
-      for (int i = k - 2; i >= 0; --i) yy[i] = zt[i] - ll[i] * yy[i + 1];
-      for (int i = 0; i < k; ++i) {
-        const std::complex<double> t = cj * yy[i];
-        g[(size_t)r * o.max_iter + i].x += t.real();
-        g[(size_t)r * o.max_iter + i].y += t.imag();
-      }
+    kr[r] = std::max(0, S[r].iter - 1);
+    bn[r] = S[r].bnorm;
+    S[r].k_final = kr[r];
+    kmax = std::max(kmax, kr[r]);
+    if (kr[r] >= 1) {
+      S[r].iter = 1;
+      S[r].done = 0;
     }
-    S[r].iter = 1;
-    S[r].done = 0;
   }
+  std::vector<double2> g;
+  lanczos_sum_coefficients(ctx, nsrc, kr, bn, ha, hb, o.max_iter, g);
   e = cudaMemcpyAsync(gco, g.data(), sizeof(double2) * g.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(w.a.src, S.data(), sizeof(SrcState) * nsrc, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.a.cnt, 0, sizeof(unsigned) * 2 * nsrc, s);
