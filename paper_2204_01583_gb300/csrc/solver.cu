@@ -14,7 +14,8 @@
 //     z_j - T_k, updated one row per step:
 //       d_1 = z - alpha_1,  d_i = z - alpha_i - beta_{i-1}^2 / d_{i-1},
 //       l_i = -beta_i / d_i,  omega_1 = ||b||,  omega_i = -l_{i-1} omega_{i-1},
-//       zeta_i = omega_i / d_i;
+//       zeta_i = omega_i / d_i
+//     (1 / d_i is kept, so each step costs one real division per node);
 //     |Im d_i| >= |Im z| > 0, so no pivot ever vanishes (no breakdown);
 //   * per node the direction p_i = v_i - l_{i-1} p_{i-1} and y += zeta_i p_i, so that
 //     the weighted sum of Eq. 7, s = c0 b + sum_j c_j y_j, is accumulated directly;
@@ -44,6 +45,7 @@ constexpr int NT2 = 256;  // K2: vector updates
 
 struct SrcState {
   double bnorm;   // ||b||
+  double inv_b2;  // 1 / ||b||^2
   double n_prev;  // ||U_{i-1}||
   double n_cur;   // ||U_i||
   double alpha;   // alpha_i
@@ -57,8 +59,8 @@ struct SrcState {
 };
 
 struct ShiftState {
-  double2 d, omega, zeta, l;
-  double res;
+  double2 invd, omega, zeta;  // 1 / d_i, omega_i, zeta_i of the LDL^T recurrence
+  double res2;                // |beta_i zeta_i|^2 / ||b||^2 (squared relative FOM residual)
   int active;
   int last_iter;
 };
@@ -103,10 +105,6 @@ struct SolveArgs {
   R diag;
 };
 
-__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
-  const double den = b.x * b.x + b.y * b.y;
-  return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
-}
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -174,8 +172,9 @@ __device__ __forceinline__ int block_rank(bool flag, int* total, int* wsh) {
 // K1: w = H U_i / n_i - (n_i / n_{i-1}) U_{i-1};  alpha_i = Re <U_i, w> / n_i; then,
 // in the last block, row i of every active node's LDL^T and the active list for K2.
 // The stencil runs 4 threads per site (hw_split_*): a block covers 32 sites.
+// 4 blocks per SM (<= 128 registers): an 8^4 x 4-source grid (512 blocks) fits one wave
 template <typename R>
-__global__ void __launch_bounds__(NT1) lanczos_hw_kernel(SolveArgs<R> a) {
+__global__ void __launch_bounds__(NT1, 4) lanczos_hw_kernel(SolveArgs<R> a) {
   using T = typename Store<R>::T;
   __shared__ double sh[NT1 / 32];
   __shared__ int wsh[NT1 / 32];
@@ -270,13 +269,16 @@ __global__ void __launch_bounds__(NT1) lanczos_hw_kernel(SolveArgs<R> a) {
           d = make_double2(zj.x - alpha, zj.y);
           om = make_double2(S->bnorm, 0.0);
         } else {
-          const double2 t = cdiv(make_double2(beta_prev * beta_prev, 0.0), q.d);
-          d = make_double2(zj.x - alpha - t.x, zj.y - t.y);
-          lprev = q.l;
+          const double2 ip = q.invd;  // 1 / d_{i-1}
+          lprev = make_double2(-beta_prev * ip.x, -beta_prev * ip.y);
+          const double b2 = beta_prev * beta_prev;
+          d = make_double2(zj.x - alpha - b2 * ip.x, zj.y - b2 * ip.y);
           om = cmul(make_double2(-lprev.x, -lprev.y), q.omega);
         }
-        zeta = cdiv(om, d);
-        q.d = d;
+        const double inv = 1.0 / (d.x * d.x + d.y * d.y);
+        const double2 invd = make_double2(d.x * inv, -d.y * inv);
+        zeta = cmul(om, invd);
+        q.invd = invd;
         q.omega = om;
         q.zeta = zeta;
       }
@@ -383,7 +385,8 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
   const double beta = beta_sh;
   if (!isfinite(beta)) return;
   const double tol = a.tol_src ? a.tol_src[r] : a.prm->tol;
-  const double bnorm = S->bnorm;
+  const double tol2 = tol * tol;
+  const double b2n = beta * beta * S->inv_b2;
   int still = 0;
   for (int j0 = 0; j0 < ns; j0 += NT2) {
     const int j = j0 + threadIdx.x;
@@ -391,12 +394,11 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
     if (j < ns) {
       ShiftState& q = a.sh[(size_t)r * ns + j];
       if (q.active) {
-        q.res = beta * sqrt(q.zeta.x * q.zeta.x + q.zeta.y * q.zeta.y) / bnorm;
-        q.l = cdiv(make_double2(-beta, 0.0), q.d);
+        q.res2 = b2n * (q.zeta.x * q.zeta.x + q.zeta.y * q.zeta.y);
         q.last_iter = i;
-        if (q.res <= tol || beta == 0.0) {
+        if (q.res2 <= tol2 || beta == 0.0) {
           q.active = 0;
-          if (beta == 0.0) q.res = 0.0;
+          if (beta == 0.0) q.res2 = 0.0;
         } else {
           act = true;
         }
@@ -421,7 +423,7 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
 // alpha_i and ||U_i|| with the first pass's arithmetic, and add g_i v_i to the sum.
 // One kernel per iteration; the last block advances the iteration counter.
 template <typename R>
-__global__ void __launch_bounds__(NT1) lanczos_regen_kernel(SolveArgs<R> a) {
+__global__ void __launch_bounds__(NT1, 4) lanczos_regen_kernel(SolveArgs<R> a) {
   using T = typename Store<R>::T;
   __shared__ bool last;
   __shared__ Cx<R> sm[4 * 12 * kSplitSites];
@@ -532,6 +534,7 @@ __global__ void __launch_bounds__(NT2) lanczos_init_kernel(SolveArgs<R> a, const
   a.cnt[2 * r + 1] = 0;
   SrcState* S = a.src + r;
   S->bnorm = sqrt(tot);
+  S->inv_b2 = tot > 0.0 ? 1.0 / tot : 0.0;
   S->n_cur = S->bnorm;
   S->n_prev = 1.0;
   S->alpha = 0.0;
@@ -544,8 +547,8 @@ __global__ void __launch_bounds__(NT2) lanczos_init_kernel(SolveArgs<R> a, const
   const int ns = a.prm->nshift;
   for (int j = 0; j < ns; ++j) {
     ShiftState& q = a.sh[(size_t)r * ns + j];
-    q.d = q.omega = q.zeta = q.l = make_double2(0.0, 0.0);
-    q.res = 1.0;
+    q.invd = q.omega = q.zeta = make_double2(0.0, 0.0);
+    q.res2 = 1.0;
     q.active = 1;
     q.last_iter = 0;
   }
@@ -555,7 +558,7 @@ __global__ void __launch_bounds__(NT2) lanczos_init_kernel(SolveArgs<R> a, const
   if (skip || !(S->bnorm > 0.0) || !isfinite(S->bnorm)) {
     for (int j = 0; j < ns; ++j) {
       a.sh[(size_t)r * ns + j].active = 0;
-      a.sh[(size_t)r * ns + j].res = 0.0;
+      a.sh[(size_t)r * ns + j].res2 = 0.0;
     }
     mark_done(S, a.done_count, (skip || isfinite(S->bnorm)) ? OV_OK : OV_ERR_BREAKDOWN);
   }
@@ -771,9 +774,10 @@ int finish_solve(ov_ctx* ctx, SolveWs<R>& w, int nsrc, int ns, const std::vector
     double bound = 0.0;
     for (int j = 0; j < ns; ++j) {
       const ShiftState& q = Q[(size_t)r * ns + j];
-      so->max_residual = std::max(so->max_residual, q.res);
+      const double res = std::sqrt(q.res2);
+      so->max_residual = std::max(so->max_residual, res);
       const double2 zz = zh[(size_t)r * ns + j], cc = ch[(size_t)r * ns + j];
-      bound += std::hypot(cc.x, cc.y) * q.res / std::fabs(zz.y);
+      bound += std::hypot(cc.x, cc.y) * res / std::fabs(zz.y);
     }
     so->error_bound = std::max(so->error_bound, bound);
   }
