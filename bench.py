@@ -394,7 +394,9 @@ def run_ours(args, wl):
 #                          + p = v - l p and s += c zeta p (12 x 16 flop; p read+write 384 B) per nu
 #   lanczos_regen_kernel:  stencil + Lanczos update + s += g v (1368 + 12 x 24 flop;
 #                          576 + 4 x 192 B + sum read+write 384 B)            per si
+#   lanczos_coop_kernel:   the two above for every iteration in one persistent launch  per si
 FP64_WORK = {
+    "lanczos_coop_kernel": {"si": (1560.0, 1728.0)},
     "lanczos_hw_kernel": {"si": (1440.0, 1152.0)},
     "lanczos_update_kernel": {"si": (120.0, 576.0), "nu": (192.0, 384.0)},
     "lanczos_regen_kernel": {"si": (1656.0, 1728.0)},

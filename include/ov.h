@@ -204,6 +204,13 @@ int ov_overlap_vjp(ov_ctx* ctx, double m_q, const void* eta, const void* b, void
 int ov_set_hw32_variant(ov_ctx* ctx, int k);
 int ov_hw32_variants(int k, int* rhs_tile, int* compressed, int* threads);
 
+/* enable = 1: the coefficient-space FP64 solve runs its whole iteration loop as one
+ * cooperative persistent launch when the grid fits on the GPU (up to 16 sources);
+ * enable = 0 (default): one launch per iteration phase, replayed from CUDA graphs
+ * (measured faster on GB300 at 8^4: two grid barriers per iteration and L2-only
+ * neighbour loads cost more than the launches and reduction tails they remove). */
+int ov_set_persistent(ov_ctx* ctx, int enable);
+
 /* Kernel timing: when enabled, the library brackets every launch of its main
  * kernel classes with CUDA events on the launching stream and accumulates their
  * durations.  ov_kernel_times fills up to `cap` entries (name pointer, launches,

@@ -11,7 +11,7 @@
 
 const char* const kKernelClassNames[KC_COUNT] = {"hw_kernel",         "lanczos_hw_kernel", "lanczos_update_kernel",
                                                   "layout_kernels",    "init_kernels",      "force_kernel",
-                                                  "residual_kernels",  "lanczos_regen_kernel"};
+                                                  "residual_kernels",  "lanczos_regen_kernel", "lanczos_coop_kernel"};
 
 // ------------------------------------------------------------ utilities
 
@@ -664,6 +664,12 @@ int ov_hw32_variants(int k, int* rhs_tile, int* compressed, int* threads) {
     *threads = 128;
   }
   return n + 1;
+}
+
+int ov_set_persistent(ov_ctx* ctx, int enable) {
+  if (!ctx) return OV_ERR_INVALID_ARG;
+  ctx->no_coop = (enable == 0);
+  return OV_OK;
 }
 
 int ov_set_kernel_timing(ov_ctx* ctx, int enable) {

@@ -15,9 +15,12 @@ template <typename R> struct Store;
 template <> struct Store<double> { using T = double2; };
 template <> struct Store<float> { using T = float2; };
 
-template <typename R>
+// Loads: CG = false reads through the read-only (non-coherent) path, for data no block
+// writes during the launch; CG = true reads from L2 (ld.global.cg), for data other blocks
+// of a persistent launch wrote before a grid barrier.
+template <typename R, bool CG = false>
 __device__ __forceinline__ Cx<R> ld(const typename Store<R>::T* p) {
-  typename Store<R>::T v = __ldg(p);
+  typename Store<R>::T v = CG ? __ldcg(p) : __ldg(p);
   return {v.x, v.y};
 }
 template <typename R>
@@ -107,7 +110,7 @@ __device__ __forceinline__ void mulAdag(Cx<R> h0, Cx<R> h1, Cx<R>& a0, Cx<R>& a1
 // One direction of the hopping term, both hops, accumulated into acc[12]
 // (acc -= 1/2 [(1 - g) U psi(x+mu) + (1 + g) U(x-mu)^dag psi(x-mu)]).
 // in: spinor planes, element (k, site) at in[k * V + site]; U: link planes.
-template <int MU, typename R>
+template <int MU, typename R, bool CG = false>
 __device__ __forceinline__ void hop_dir(const typename Store<R>::T* __restrict__ in,
                                         const typename Store<R>::T* __restrict__ U, const Geom& g,
                                         int s, const int c[4], Cx<R> acc[12]) {
@@ -121,10 +124,10 @@ __device__ __forceinline__ void hop_dir(const typename Store<R>::T* __restrict__
     Cx<R> h0[3], h1[3];
 #pragma unroll
     for (int col = 0; col < 3; ++col) {
-      Cx<R> p0 = ld<R>(in + (0 * 3 + col) * (size_t)V + sn);
-      Cx<R> p1 = ld<R>(in + (1 * 3 + col) * (size_t)V + sn);
-      Cx<R> p2 = ld<R>(in + (2 * 3 + col) * (size_t)V + sn);
-      Cx<R> p3 = ld<R>(in + (3 * 3 + col) * (size_t)V + sn);
+      Cx<R> p0 = ld<R, CG>(in + (0 * 3 + col) * (size_t)V + sn);
+      Cx<R> p1 = ld<R, CG>(in + (1 * 3 + col) * (size_t)V + sn);
+      Cx<R> p2 = ld<R, CG>(in + (2 * 3 + col) * (size_t)V + sn);
+      Cx<R> p3 = ld<R, CG>(in + (3 * 3 + col) * (size_t)V + sn);
       Cx<R> a0, a1;
       mulA<MU>(p2, p3, a0, a1);
       if (dir == 0) { h0[col] = csub(p0, a0); h1[col] = csub(p1, a1); }
@@ -213,7 +216,7 @@ __device__ __forceinline__ double sum_partials(const double* p, int n, double* s
 constexpr int kSplitNT = 128;
 constexpr int kSplitSites = 32;
 
-template <typename R>
+template <typename R, bool CG = false>
 __device__ __forceinline__ void hw_split_phase1(const typename Store<R>::T* __restrict__ in,
                                                 const typename Store<R>::T* __restrict__ U, const Geom& g,
                                                 int site0, Cx<R>* sm) {
@@ -226,10 +229,10 @@ __device__ __forceinline__ void hw_split_phase1(const typename Store<R>::T* __re
     int c[4];
     site_coords(g, s, c);
     switch (mu) {  // warp-uniform
-      case 0: hop_dir<0, R>(in, U, g, s, c, acc); break;
-      case 1: hop_dir<1, R>(in, U, g, s, c, acc); break;
-      case 2: hop_dir<2, R>(in, U, g, s, c, acc); break;
-      default: hop_dir<3, R>(in, U, g, s, c, acc); break;
+      case 0: hop_dir<0, R, CG>(in, U, g, s, c, acc); break;
+      case 1: hop_dir<1, R, CG>(in, U, g, s, c, acc); break;
+      case 2: hop_dir<2, R, CG>(in, U, g, s, c, acc); break;
+      default: hop_dir<3, R, CG>(in, U, g, s, c, acc); break;
     }
   }
 #pragma unroll
@@ -238,7 +241,7 @@ __device__ __forceinline__ void hw_split_phase1(const typename Store<R>::T* __re
 
 // Phase 2 for this thread's three components kk = 3 (t >> 5) + {0, 1, 2}; call after
 // __syncthreads().  Returns false for sites beyond V.
-template <typename R>
+template <typename R, bool CG = false>
 __device__ __forceinline__ bool hw_split_phase2(const typename Store<R>::T* __restrict__ in, const Geom& g,
                                                 int site0, R diag, const Cx<R>* sm, Cx<R> o[3], int* s_out,
                                                 int* k0_out) {
@@ -250,7 +253,7 @@ __device__ __forceinline__ bool hw_split_phase2(const typename Store<R>::T* __re
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     const int k = 3 * grp + q;
-    Cx<R> v = cscale(diag, ld<R>(in + k * (size_t)g.V + s));
+    Cx<R> v = cscale(diag, ld<R, CG>(in + k * (size_t)g.V + s));
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) v = cadd(v, sm[(mu * 12 + k) * kSplitSites + lane]);
     o[q] = (k >= 6) ? cneg(v) : v;

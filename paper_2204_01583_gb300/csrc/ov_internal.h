@@ -48,6 +48,7 @@ enum KernelClass {
   KC_FORCE,          // link force
   KC_RESIDUAL,       // FP64 true residuals (mixed mode)
   KC_REGEN,          // second pass of the two-pass mode
+  KC_COOP,           // persistent cooperative Lanczos loop
   KC_COUNT
 };
 
@@ -81,6 +82,7 @@ struct ov_ctx {
   bool have_b32 = false;               // broadcast FP32 links for the paired layout ("gauge.b32")
   std::map<int, int> hw32_choice;      // nrhs -> autotuned FP32 stencil variant
   int hw32_force = -1;                 // ov_set_hw32_variant
+  bool no_coop = true;                 // ov_set_persistent(ctx, 1) enables the persistent loop
 
   // quadrature S_N = c0 + sum_j c_j (z_j - H)^-1
   std::vector<double2> z, c;

@@ -36,6 +36,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace {
@@ -476,6 +478,203 @@ __global__ void __launch_bounds__(NT1, 4) lanczos_regen_kernel(SolveArgs<R> a) {
   }
 }
 
+// The whole Lanczos loop of the scalar-only forms (vec_shifts = 0) as one cooperative
+// persistent launch.  Per iteration: stencil phase (w and <U_i, w> partials), grid
+// barrier, every block reduces the same partials in the same order (so every block
+// holds the same alpha_i: no serial last-block step), vector update (U_{i+1} and
+// ||U_{i+1}||^2 partials), grid barrier, beta_i, and each thread of the grid advances
+// at most one node's LDL^T recurrence.  A source whose nodes have all met tol is
+// retired at the next barrier (it spends one extra stencil phase).  Data that other
+// blocks write during the launch is read through L2 (ld.global.cg).
+constexpr int kCoopMaxSrc = 16;
+
+template <typename R>
+__global__ void __launch_bounds__(NT1, 4) lanczos_coop_kernel(SolveArgs<R> a, int nsrc) {
+  namespace cg = cooperative_groups;
+  using T = typename Store<R>::T;
+  cg::grid_group grid = cg::this_grid();
+  __shared__ Cx<R> sm[4 * 12 * kSplitSites];
+  __shared__ double sh[NT1 / 32];
+  __shared__ double s_part[kCoopMaxSrc], s_alpha[kCoopMaxSrc], s_beta[kCoopMaxSrc];
+  __shared__ double s_ncur[kCoopMaxSrc], s_nprev[kCoopMaxSrc];
+  __shared__ int s_done[kCoopMaxSrc];
+  __shared__ int s_stop;
+  const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+  const int V = a.g.V;
+  const size_t n12 = (size_t)12 * V;
+  const int ntile = (V + kSplitSites - 1) / kSplitSites;
+  const int nwork = ntile * nsrc;
+  const int ns = a.prm->nshift, mi = a.prm->max_iter;
+  const size_t nsl = (size_t)a.prm->nslots;
+  const int lane = tid & 31, grp = tid >> 5;
+  if (tid < nsrc) {
+    s_ncur[tid] = a.src[tid].n_cur;
+    s_nprev[tid] = a.src[tid].n_prev;
+    s_done[tid] = a.src[tid].done;
+  }
+  __syncthreads();
+  for (int i = 1;; ++i) {
+    // ---- phase 1: w = H U_i / n_i - (n_i / n_{i-1}) U_{i-1}, partial <U_i, w>
+    if (tid < kCoopMaxSrc) s_part[tid] = 0.0;
+    __syncthreads();
+    if (i <= mi) {
+      for (int wk = b; wk < nwork; wk += G) {
+        const int r = wk / ntile, site0 = (wk % ntile) * kSplitSites;
+        if (s_done[r]) continue;
+        const T* base = a.ring + (size_t)r * nsl * n12;
+        const T* Ui = base + lz_slot(a.prm, i) * n12;
+        const T* Um = base + (a.prm->store ? (size_t)(i - 1) : (size_t)((i + 2) % 3)) * n12;
+        T* W = (T*)base + lz_slot(a.prm, i + 1) * n12;
+        const double inv_n = 1.0 / s_ncur[r];
+        const double cm = (i > 1) ? s_ncur[r] / s_nprev[r] : 0.0;
+        hw_split_phase1<R, true>(Ui, a.U, a.g, site0, sm);
+        __syncthreads();
+        Cx<R> o[3];
+        int s, k0;
+        double dot = 0.0;
+        if (hw_split_phase2<R, true>(Ui, a.g, site0, a.diag, sm, o, &s, &k0)) {
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const size_t e = (k0 + q) * (size_t)V + s;
+            const Cx<R> u = ld<R, true>(Ui + e);
+            const Cx<R> um = (i > 1) ? ld<R, true>(Um + e) : Cx<R>{R(0), R(0)};
+            const Cx<R> w = lz_w<R>(o[q], um, (R)inv_n, (R)cm, i == 1);
+            st<R>(W + e, w);
+            dot += (double)u.re * (double)w.re + (double)u.im * (double)w.im;
+          }
+        }
+        const double bs = block_sum<NT1>(dot, sh);
+        if (tid == 0) s_part[r] += bs;
+        __syncthreads();
+      }
+    }
+    if (tid < nsrc) a.part1[(size_t)tid * G + b] = s_part[tid];
+    grid.sync();
+    // ---- retire sources whose nodes all met tol at iteration i - 1
+    if (i > 1) {
+      for (int r = 0; r < nsrc; ++r) {
+        if (s_done[r]) continue;
+        int act = 0;
+        for (int j0 = 0; j0 < ns; j0 += NT1) {
+          const int j = j0 + tid;
+          const int f = (j < ns) ? __ldcg(&a.sh[(size_t)r * ns + j].active) : 0;
+          act += __syncthreads_count(f);
+        }
+        const bool beta0 = (s_ncur[r] == 0.0);
+        if (act == 0 || beta0 || i > mi) {
+          if (tid == 0) {
+            s_done[r] = 1;
+            if (b == 0) {
+              SrcState* S = a.src + r;
+              S->iter = i;
+              S->n_cur = s_ncur[r];
+              S->n_prev = s_nprev[r];
+              S->status = (act > 0 && !beta0) ? OV_ERR_NOT_CONVERGED : OV_OK;
+              S->done = 1;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (tid == 0) {
+      int all = 1;
+      for (int r = 0; r < nsrc; ++r) all &= s_done[r];
+      s_stop = all;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    // ---- alpha_i for every source (same order in every block)
+    for (int r = 0; r < nsrc; ++r) {
+      const double t = sum_partials<NT1>(a.part1 + (size_t)r * G, G, sh);
+      if (tid == 0) s_alpha[r] = t / s_ncur[r];
+    }
+    __syncthreads();
+    // ---- phase 2: U_{i+1} = w - alpha_i v_i (in place), partial ||U_{i+1}||^2
+    if (tid < kCoopMaxSrc) s_part[tid] = 0.0;
+    __syncthreads();
+    for (int wk = b; wk < nwork; wk += G) {
+      const int r = wk / ntile, site0 = (wk % ntile) * kSplitSites;
+      if (s_done[r]) continue;
+      const T* base = a.ring + (size_t)r * nsl * n12;
+      const T* Ui = base + lz_slot(a.prm, i) * n12;
+      T* W = (T*)base + lz_slot(a.prm, i + 1) * n12;
+      const double inv_n = 1.0 / s_ncur[r];
+      const int s = site0 + lane;
+      double nrm = 0.0;
+      if (s < V) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const size_t e = (3 * grp + q) * (size_t)V + s;
+          const Cx<R> v = lz_v<R>(ld<R, true>(Ui + e), (R)inv_n);
+          const Cx<R> u = lz_next<R>(ld<R, true>(W + e), v, (R)s_alpha[r]);
+          st<R>(W + e, u);
+          nrm += (double)u.re * (double)u.re + (double)u.im * (double)u.im;
+        }
+      }
+      const double bs = block_sum<NT1>(nrm, sh);
+      if (tid == 0) s_part[r] += bs;
+      __syncthreads();
+    }
+    if (tid < nsrc) a.part2[(size_t)tid * G + b] = s_part[tid];
+    grid.sync();
+    for (int r = 0; r < nsrc; ++r) {
+      const double t = sum_partials<NT1>(a.part2 + (size_t)r * G, G, sh);
+      if (tid == 0) s_beta[r] = sqrt(t);
+    }
+    __syncthreads();
+    // ---- node recurrences (one node per thread of the grid) and history
+    for (int q = b * NT1 + tid; q < nsrc * ns; q += G * NT1) {
+      const int r = q / ns;
+      if (s_done[r]) continue;
+      ShiftState& st8 = a.sh[q];
+      if (!st8.active) continue;
+      const double alpha = s_alpha[r], beta = s_beta[r], beta_prev = s_ncur[r];
+      const double2 zj = a.z[q];
+      double2 d, om;
+      if (i == 1) {
+        d = make_double2(zj.x - alpha, zj.y);
+        om = make_double2(a.src[r].bnorm, 0.0);
+      } else {
+        const double2 ip = st8.invd;
+        const double b2 = beta_prev * beta_prev;
+        d = make_double2(zj.x - alpha - b2 * ip.x, zj.y - b2 * ip.y);
+        om = cmul(make_double2(beta_prev * ip.x, beta_prev * ip.y), st8.omega);
+      }
+      const double inv = 1.0 / (d.x * d.x + d.y * d.y);
+      const double2 invd = make_double2(d.x * inv, -d.y * inv);
+      const double2 zeta = cmul(om, invd);
+      st8.invd = invd;
+      st8.omega = om;
+      st8.zeta = zeta;
+      const double tol = a.tol_src ? a.tol_src[r] : a.prm->tol;
+      st8.res2 = beta * beta * a.src[r].inv_b2 * (zeta.x * zeta.x + zeta.y * zeta.y);
+      st8.last_iter = i;
+      if (st8.res2 <= tol * tol || beta == 0.0) {
+        st8.active = 0;
+        if (beta == 0.0) st8.res2 = 0.0;
+      }
+    }
+    if (tid < nsrc && !s_done[tid]) {
+      if (b == 0 && a.hist_a) {
+        a.hist_a[(size_t)tid * mi + (i - 1)] = s_alpha[tid];
+        a.hist_b[(size_t)tid * mi + (i - 1)] = s_beta[tid];
+      }
+      s_nprev[tid] = s_ncur[tid];
+      s_ncur[tid] = s_beta[tid];
+      if (!isfinite(s_alpha[tid]) || !isfinite(s_beta[tid])) {
+        s_done[tid] = 1;
+        if (b == 0) {
+          a.src[tid].iter = i + 1;
+          a.src[tid].status = OV_ERR_BREAKDOWN;
+          a.src[tid].done = 1;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Stored-basis variant of the second pass: sum[r][e] += sum_{i=1..k_r} gw[r][i-1] U_i[e],
 // gw = g_i / ||U_i|| (the basis is stored unnormalised).  Reads the basis once.
 __global__ void basis_sum_kernel(const double2* __restrict__ basis, int nslots, const double2* __restrict__ gw,
@@ -720,6 +919,41 @@ int run_iterations(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, int nshift, int f
   return OV_OK;
 }
 
+// The persistent form of the iteration loop (lanczos_coop_kernel) when it applies:
+// scalar-only node recurrences, at most kCoopMaxSrc sources, and a grid that is
+// co-resident (one block per 32-site tile and source, capped by occupancy).  Returns
+// OV_ERR_INVALID_ARG (nothing launched) when it does not apply.
+template <typename R>
+int run_coop(ov_ctx* ctx, SolveWs<R>& w, int nsrc, cudaStream_t s, double* launches) {
+  if (nsrc > kCoopMaxSrc || ctx->no_coop) return OV_ERR_INVALID_ARG;
+  int dev = 0, coop = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (!coop) return OV_ERR_INVALID_ARG;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_coop_kernel<R>, NT1, 0) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return OV_ERR_INVALID_ARG;
+  }
+  const int ntile = (ctx->g.V + kSplitSites - 1) / kSplitSites;
+  const int G = std::min(per_sm * nsm, ntile * nsrc);
+  SolveArgs<R> a = w.a;
+  // block partials, indexed source * G + block
+  int st = OV_OK;
+  a.part1 = (double*)ws_get(ctx, "coop.part1", sizeof(double) * (size_t)G * nsrc, &st);
+  a.part2 = (double*)ws_get(ctx, "coop.part2", sizeof(double) * (size_t)G * nsrc, &st);
+  if (st != OV_OK) return st;
+  void* args[] = {(void*)&a, (void*)&nsrc};
+  cudaEvent_t ev;
+  kt_begin(ctx, KC_COOP, s, &ev);
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)lanczos_coop_kernel<R>, dim3(G), dim3(NT1), args, 0, s);
+  kt_end(ctx, KC_COOP, s, ev);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaLaunchCooperativeKernel");
+  *launches += 1.0;
+  return OV_OK;
+}
+
 template <typename R>
 int init_solve(ov_ctx* ctx, SolveWs<R>& w, const double2* b_soa, int nsrc, int ns,
                const std::vector<double2>& zh, const std::vector<double2>& ch, double2 c0,
@@ -875,7 +1109,7 @@ static int solve_sign_stored(ov_ctx* ctx, const double2* b_soa, double2* out_soa
   const int ns = (int)ctx->z.size();
   const size_t n12 = (size_t)12 * ctx->g.V;
   SolveWs<double> w;
-  int st = setup_ws<double>(ctx, nsrc, ns, false, true, true, cap, &w, "fp64s", cap + 2);
+  int st = setup_ws<double>(ctx, nsrc, ns, false, true, true, cap, &w, "fp64s", cap + 3);
   if (st != OV_OK) return st;
   std::vector<double2> zh((size_t)nsrc * ns), ch((size_t)nsrc * ns);
   for (int r = 0; r < nsrc; ++r)
@@ -886,7 +1120,8 @@ static int solve_sign_stored(ov_ctx* ctx, const double2* b_soa, double2* out_soa
   st = init_solve<double>(ctx, w, b_soa, nsrc, ns, zh, ch, ctx->c0, o.tol, cap, s, 0);
   if (st != OV_OK) return st;
   double launches = 1.0;
-  st = run_iterations<double>(ctx, w, nsrc, ns, 6, cap, o, s, &launches);
+  st = run_coop<double>(ctx, w, nsrc, s, &launches);
+  if (st == OV_ERR_INVALID_ARG) st = run_iterations<double>(ctx, w, nsrc, ns, 6, cap, o, s, &launches);
   if (st != OV_OK) return st;
   const int fst = finish_solve<double>(ctx, w, nsrc, ns, zh, ch, so, s);
   // not converged within the store: the caller regenerates, unless the store already
@@ -921,7 +1156,7 @@ static int solve_sign_stored(ov_ctx* ctx, const double2* b_soa, double2* out_soa
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy coefficients");
   cudaEvent_t ev;
   kt_begin(ctx, KC_REGEN, s, &ev);
-  basis_sum_kernel<<<dim3((unsigned)((n12 + 255) / 256), nsrc), 256, 0, s>>>(w.a.ring, cap + 2, gd, cap, krd,
+  basis_sum_kernel<<<dim3((unsigned)((n12 + 255) / 256), nsrc), 256, 0, s>>>(w.a.ring, cap + 3, gd, cap, krd,
                                                                              w.a.sacc, n12);
   kt_end(ctx, KC_REGEN, s, ev);
   OV_CHECK_LAUNCH(ctx, "basis_sum_kernel");

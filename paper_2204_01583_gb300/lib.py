@@ -36,7 +36,7 @@ EXPORTS = (
     "ov_create", "ov_destroy", "ov_last_error", "ov_set_gauge", "ov_apply_HW", "ov_set_contour",
     "ov_set_contour_ellipse", "ov_get_contour", "ov_place_contour", "ov_sgn_HW_apply", "ov_overlap_apply",
     "ov_sgn_vjp", "ov_overlap_vjp", "ov_set_kernel_timing", "ov_kernel_times", "ov_version",
-    "ov_apply_HW_noalloc", "ov_set_hw32_variant", "ov_hw32_variants",
+    "ov_apply_HW_noalloc", "ov_set_hw32_variant", "ov_hw32_variants", "ov_set_persistent",
 )
 
 
@@ -89,6 +89,7 @@ def _load():
         "ov_kernel_times": [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong), dp, i],
         "ov_apply_HW_noalloc": [ip, i, d, vp, vp, vp, i, vp],
         "ov_set_hw32_variant": [vp, i],
+        "ov_set_persistent": [vp, i],
         "ov_hw32_variants": [i, ip, ip, ip],
     }
     for name, args in sig.items():
@@ -244,6 +245,9 @@ class Context:
                                  ctypes.byref(st), _stream_ptr(stream))
         self._check(rc)
         return st.as_dict()
+
+    def set_persistent(self, enable=True):
+        self._check(_lib.ov_set_persistent(self._h, int(bool(enable))))
 
     def set_hw32_variant(self, k=-1):
         self._check(_lib.ov_set_hw32_variant(self._h, int(k)))

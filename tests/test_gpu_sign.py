@@ -95,9 +95,12 @@ def test_two_pass_equals_shifted(gpu_lib, config2, mode):
     ctx, U, b, spec, want0 = config2
     a, sa = sgn_gpu(ctx, b, nrhs=4, tol=1e-12, mode="fp64")
     c, sc = sgn_gpu(ctx, b, nrhs=4, tol=1e-12, mode=mode)
-    assert sa["iterations"] == sc["iterations"]
+    # the reductions are grouped differently, so alpha/beta differ in the last bits and the
+    # stopping iteration near tol = 1e-12 moves by a few percent; the results agree to
+    # the solver accuracy
+    assert abs(sa["iterations"] - sc["iterations"]) <= 0.15 * sa["iterations"]
     for k in range(4):
-        assert rel(c[k], a[k]) < 1e-12
+        assert rel(c[k], a[k]) < 1e-11
     assert sc["node_updates"] == 0 and sa["node_updates"] > 0
 
 
@@ -210,3 +213,18 @@ def test_edge_cases(gpu_lib, mode):
     with pytest.raises(gpu_lib.OvError) as e:
         ctx2.sgn(bd, out, 1)
     assert e.value.code == gpu_lib.OV_ERR_NO_CONTOUR
+
+
+def test_persistent_and_per_iteration_launches_agree(gpu_lib, config2):
+    """The cooperative persistent loop and the per-iteration (graph) kernels run the same
+    recurrences (partial sums grouped differently): results agree to solver accuracy."""
+    ctx, U, b, spec, want0 = config2
+    ctx.set_persistent(True)
+    a, sa = sgn_gpu(ctx, b, nrhs=4, tol=1e-12, mode="fp64_2pass")
+    ctx.set_persistent(False)
+    c, sc = sgn_gpu(ctx, b, nrhs=4, tol=1e-12, mode="fp64_2pass")
+    assert abs(sa["iterations"] - sc["iterations"]) <= 0.15 * sc["iterations"]
+    assert sa["launches"] < sc["launches"]
+    for k in range(4):
+        assert rel(a[k], c[k]) < 1e-11
+    assert rel(a[0], want0) < 1e-10
