@@ -520,7 +520,8 @@ def run_dslash(args, wl):
         torch.cuda.synchronize()
         n, ms = ctx.kernel_times()["hw_kernel"]
         ctx.set_kernel_timing(False)
-        link_reals = {0: 72, 1: 48, 2: 144}[comp]  # plain, 12-real compressed, broadcast (re,re,im,im)
+        # plain, 12-real, broadcast (re,re,im,im), padded float4 pairs (5 per link), 12-real float4
+        link_reals = {0: 72, 1: 48, 2: 144, 3: 80, 4: 48}[comp]
         by = V * (link_reals * s_real + nrhs * 48 * s_real)  # links once per launch; each RHS in + out
         per = ms / n / 1e3
         rows.append({"variant": k, "rhs_tile": rt, "compressed_links": bool(comp), "threads": nt,
@@ -542,7 +543,7 @@ def run_dslash(args, wl):
             "config": {"workload": args.workload, "lattice": "x".join(map(str, dims)), "rhs": nrhs,
                        "l2": "256 MiB buffer written between launches",
                        "bytes": "links once per launch at their stored size (72 reals/site; 48 compressed; "
-                                "144 broadcast) + 48 reals/site per RHS in and out"},
+                                "144 broadcast; 80 padded pairs) + 48 reals/site per RHS in and out"},
             "clocks": clocks, "roofline": roof, "variants": rows}
     print(json.dumps(line), flush=True)
     return 0

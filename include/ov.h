@@ -198,9 +198,10 @@ int ov_overlap_vjp(ov_ctx* ctx, double m_q, const void* eta, const void* b, void
  * them), 12-real link compression (row 2 rebuilt as conj(row0 x row1)) and block
  * size.  k = -1 (default): autotune -- each variant is timed once on the live data per
  * right-hand-side count and the fastest is kept.  ov_hw32_variants returns the number
- * of variants and, for 0 <= k < count, describes variant k; the last one
- * (compressed = 2) is the right-hand-side-paired layout computed with paired FP32
- * instructions and broadcast links. */
+ * of variants and, for 0 <= k < count, describes variant k.  compressed: 0 plain
+ * links, 1 12-real links (structure-of-arrays float2 layout); 2 right-hand-side-paired
+ * layout with paired FP32 instructions and broadcast links; 3 and 4 spin-paired float4
+ * layout (one 16-byte load per spin pair) with plain (padded) or 12-real links. */
 int ov_set_hw32_variant(ov_ctx* ctx, int k);
 int ov_hw32_variants(int k, int* rhs_tile, int* compressed, int* threads);
 

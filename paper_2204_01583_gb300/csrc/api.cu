@@ -284,6 +284,7 @@ int ov_set_gauge(ov_ctx* ctx, const double* U, int on_device, void* stream) {
   ctx->have_gauge = true;
   ctx->have_c32 = false;
   ctx->have_b32 = false;
+  ctx->have_s4 = false;
   return OV_OK;
 }
 
@@ -307,36 +308,57 @@ int ov_apply_HW(ov_ctx* ctx, const void* in, void* out, int nrhs, int precision,
     if ((st = launch_unpack64(ctx, b, (double2*)out, nrhs, s))) return st;
   } else {
     const int npair = (nrhs + 1) / 2;
-    const int kpair = hw32_variant_count();
+    const int kpair = hw32_variant_count();  // then kpair + 1, kpair + 2: spin-paired float4 layout
     float2* a = (float2*)ws_get(ctx, "hw.a32", sizeof(float2) * n, &st);
     float2* b = (float2*)ws_get(ctx, "hw.b32", sizeof(float2) * n, &st);
     float4* pa = (float4*)ws_get(ctx, "hw.pa32", sizeof(float4) * 12 * (size_t)ctx->g.V * npair, &st);
     float4* pb = (float4*)ws_get(ctx, "hw.pb32", sizeof(float4) * 12 * (size_t)ctx->g.V * npair, &st);
     if (st != OV_OK) return st;
+    // the S4 buffers alias the paired ones (6 float4 per site and RHS <= 12 per pair)
+    float4* sa = pa;
+    float4* sb = pb;
     int k = ctx->hw32_force;
     if (k < 0) {
       auto it = ctx->hw32_choice.find(nrhs);
       if (it != ctx->hw32_choice.end()) {
         k = it->second;
       } else {
-        // autotune: every structure-of-arrays variant and the paired kernel, on this data
+        // autotune: every structure-of-arrays variant, the paired kernel and the S4
+        // kernels, each timed on this data
         if ((st = launch_pack32(ctx, (const float2*)in, a, nrhs, s))) return st;
         int ksoa = 0;
         const float soa_ms = hw32_time_soa_variants(ctx, a, b, nrhs, s, &ksoa);
-        if ((st = launch_pack_pair32(ctx, (const float2*)in, pa, nrhs, s))) return st;
-        if ((st = launch_hw_pair(ctx, pa, pb, npair, s))) return st;  // warm (builds the links)
+        float best = soa_ms;
+        k = ksoa;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        cudaEventRecord(e0, s);
-        for (int rep = 0; rep < 3; ++rep) launch_hw_pair(ctx, pa, pb, npair, s);
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        float pms = 0.f;
-        cudaEventElapsedTime(&pms, e0, e1);
+        for (int kk = kpair; kk <= kpair + 2; ++kk) {
+          if (kk == kpair) {
+            if ((st = launch_pack_pair32(ctx, (const float2*)in, pa, nrhs, s))) return st;
+            if ((st = launch_hw_pair(ctx, pa, pb, npair, s))) return st;  // warm (builds the links)
+          } else {
+            if ((st = launch_pack_s4(ctx, (const float2*)in, sa, nrhs, s))) return st;
+            if ((st = launch_hw32_s4(ctx, sa, sb, nrhs, kk - kpair - 1, s))) return st;
+          }
+          cudaEventRecord(e0, s);
+          for (int rep = 0; rep < 3; ++rep) {
+            if (kk == kpair)
+              launch_hw_pair(ctx, pa, pb, npair, s);
+            else
+              launch_hw32_s4(ctx, sa, sb, nrhs, kk - kpair - 1, s);
+          }
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (ms / 3 < best) {
+            best = ms / 3;
+            k = kk;
+          }
+        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        k = (pms / 3 < soa_ms) ? kpair : ksoa;
         ctx->hw32_choice[nrhs] = k;
       }
     }
@@ -344,6 +366,10 @@ int ov_apply_HW(ov_ctx* ctx, const void* in, void* out, int nrhs, int precision,
       if ((st = launch_pack_pair32(ctx, (const float2*)in, pa, nrhs, s))) return st;
       if ((st = launch_hw_pair(ctx, pa, pb, npair, s))) return st;
       if ((st = launch_unpack_pair32(ctx, pb, (float2*)out, nrhs, s))) return st;
+    } else if (k > kpair) {
+      if ((st = launch_pack_s4(ctx, (const float2*)in, sa, nrhs, s))) return st;
+      if ((st = launch_hw32_s4(ctx, sa, sb, nrhs, k - kpair - 1, s))) return st;
+      if ((st = launch_unpack_s4(ctx, sb, (float2*)out, nrhs, s))) return st;
     } else {
       if ((st = launch_pack32(ctx, (const float2*)in, a, nrhs, s))) return st;
       if ((st = launch_hw32_tuned(ctx, a, b, nrhs, s, k, nullptr))) return st;
@@ -650,7 +676,7 @@ int ov_overlap_vjp(ov_ctx* ctx, double m_q, const void* eta, const void* b, void
 
 int ov_set_hw32_variant(ov_ctx* ctx, int k) {
   if (!ctx) return OV_ERR_INVALID_ARG;
-  if (k < -1 || k > hw32_variant_count()) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "no such FP32 stencil variant");
+  if (k < -1 || k > hw32_variant_count() + 2) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "no such FP32 stencil variant");
   ctx->hw32_force = k;
   return OV_OK;
 }
@@ -658,12 +684,14 @@ int ov_set_hw32_variant(ov_ctx* ctx, int k) {
 int ov_hw32_variants(int k, int* rhs_tile, int* compressed, int* threads) {
   const int n = hw32_variant_count();
   if (k >= 0 && k < n && rhs_tile && compressed && threads) hw32_variant_info(k, rhs_tile, compressed, threads);
-  if (k == n && rhs_tile && compressed && threads) {  // paired layout, FFMA2, broadcast links
-    *rhs_tile = 2;
-    *compressed = 2;
+  if (k >= n && k <= n + 2 && rhs_tile && compressed && threads) {
+    // n: right-hand-side-paired layout, paired FP32 instructions, broadcast links;
+    // n + 1, n + 2: spin-paired float4 layout with plain (padded) or 12-real links
+    *rhs_tile = (k == n) ? 2 : 1;
+    *compressed = 2 + (k - n);
     *threads = 128;
   }
-  return n + 1;
+  return n + 3;
 }
 
 int ov_set_persistent(ov_ctx* ctx, int enable) {

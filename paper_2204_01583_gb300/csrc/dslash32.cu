@@ -238,3 +238,203 @@ void hw32_variant_info(int k, int* rt, int* comp, int* nt) {
   *comp = kCands[k].comp;
   *nt = kCands[k].nt;
 }
+
+// ------------------------------------------------------------------------------------
+// Spin-paired FP32 layout ("S4"): one float4 holds (psi[s][c], psi[s+2][c]) for an upper
+// spin s in {0, 1}; element (rhs r, pair p = 3 s + c, site) at (r * 6 + p) * V + site.
+// A neighbour spinor is 6 loads of 16 bytes (the float2 layout needs 12 of 8 bytes), and
+// the addressing is 32-bit.  Links: 5 float4 per (mu, site) holding the 9 elements of U
+// row-major in pairs (the 10th slot is padding), or 3 float4 holding rows 0 and 1
+// (row 2 rebuilt as conj(row0 x row1)).
+namespace {
+
+template <bool COMP>
+__device__ __forceinline__ void load_link_s4(const float4* __restrict__ L, int mu, int V, int site,
+                                             Cx<float> U[3][3]) {
+  if (COMP) {
+    const float4* p = L + (size_t)mu * 3 * V + site;
+    const float4 a = __ldg(p), b = __ldg(p + V), c = __ldg(p + 2 * (size_t)V);
+    U[0][0] = {a.x, a.y}; U[0][1] = {a.z, a.w}; U[0][2] = {b.x, b.y};
+    U[1][0] = {b.z, b.w}; U[1][1] = {c.x, c.y}; U[1][2] = {c.z, c.w};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+      Cx<float> t = {U[0][j1].re * U[1][j2].re - U[0][j1].im * U[1][j2].im,
+                     U[0][j1].re * U[1][j2].im + U[0][j1].im * U[1][j2].re};
+      t.re -= U[0][j2].re * U[1][j1].re - U[0][j2].im * U[1][j1].im;
+      t.im -= U[0][j2].re * U[1][j1].im + U[0][j2].im * U[1][j1].re;
+      U[2][j] = {t.re, -t.im};
+    }
+  } else {
+    const float4* p = L + (size_t)mu * 5 * V + site;
+    float4 q[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) q[k] = __ldg(p + k * (size_t)V);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      const float4 v = q[e / 2];
+      U[e / 3][e % 3] = (e & 1) ? Cx<float>{v.z, v.w} : Cx<float>{v.x, v.y};
+    }
+  }
+}
+
+template <int MU, bool COMP>
+__device__ __forceinline__ void hop_dir_s4(const float4* __restrict__ in, const float4* __restrict__ L, const Geom& g,
+                                           int s, const int c[4], Cx<float> acc[12]) {
+  const int V = g.V;
+#pragma unroll
+  for (int dir = 0; dir < 2; ++dir) {
+    int sgn;
+    const int sn = dir == 0 ? nb_fwd(g, s, c, MU, &sgn) : nb_bwd(g, s, c, MU, &sgn);
+    const float4* pn = in + sn;
+    Cx<float> h0[3], h1[3];
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+      const float4 a = __ldg(pn + col * V);        // (psi0, psi2) at colour col
+      const float4 b = __ldg(pn + (3 + col) * V);  // (psi1, psi3)
+      const Cx<float> p0 = {a.x, a.y}, p2 = {a.z, a.w}, p1 = {b.x, b.y}, p3 = {b.z, b.w};
+      Cx<float> a0, a1;
+      mulA<MU>(p2, p3, a0, a1);
+      if (dir == 0) { h0[col] = csub(p0, a0); h1[col] = csub(p1, a1); }
+      else { h0[col] = cadd(p0, a0); h1[col] = cadd(p1, a1); }
+    }
+    Cx<float> U[3][3];
+    load_link_s4<COMP>(L, MU, V, dir == 0 ? s : sn, U);
+    const float f = -0.5f * (float)sgn;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Cx<float> u0 = {0.f, 0.f}, u1 = {0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        if (dir == 0) { u0 = cfma(U[i][j], h0[j], u0); u1 = cfma(U[i][j], h1[j], u1); }
+        else { u0 = cfmaconj(U[j][i], h0[j], u0); u1 = cfmaconj(U[j][i], h1[j], u1); }
+      }
+      Cx<float> b0, b1;
+      mulAdag<MU>(u0, u1, b0, b1);
+      acc[0 * 3 + i] = cadd(acc[0 * 3 + i], cscale(f, u0));
+      acc[1 * 3 + i] = cadd(acc[1 * 3 + i], cscale(f, u1));
+      if (dir == 0) {
+        acc[2 * 3 + i] = csub(acc[2 * 3 + i], cscale(f, b0));
+        acc[3 * 3 + i] = csub(acc[3 * 3 + i], cscale(f, b1));
+      } else {
+        acc[2 * 3 + i] = cadd(acc[2 * 3 + i], cscale(f, b0));
+        acc[3 * 3 + i] = cadd(acc[3 * 3 + i], cscale(f, b1));
+      }
+    }
+  }
+}
+
+template <bool COMP, int NT>
+__global__ void __launch_bounds__(NT) hw32_s4_kernel(const float4* __restrict__ in, float4* __restrict__ out,
+                                                     const float4* __restrict__ L, Geom g, float diag) {
+  const int s = blockIdx.x * NT + threadIdx.x;
+  if (s >= g.V) return;
+  const int V = g.V;
+  const float4* inr = in + (size_t)blockIdx.y * 6 * V;
+  float4* outr = out + (size_t)blockIdx.y * 6 * V;
+  Cx<float> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = {0.f, 0.f};
+  int c[4];
+  site_coords(g, s, c);
+  hop_dir_s4<0, COMP>(inr, L, g, s, c, acc);
+  hop_dir_s4<1, COMP>(inr, L, g, s, c, acc);
+  hop_dir_s4<2, COMP>(inr, L, g, s, c, acc);
+  hop_dir_s4<3, COMP>(inr, L, g, s, c, acc);
+#pragma unroll
+  for (int p = 0; p < 6; ++p) {
+    const int sp = p / 3, col = p % 3;
+    const float4 v = __ldg(inr + p * V + s);
+    // upper spin sp, lower spin sp + 2 (gamma5 = -1 on it)
+    const Cx<float> up = cadd(cscale(diag, Cx<float>{v.x, v.y}), acc[sp * 3 + col]);
+    const Cx<float> lo = cneg(cadd(cscale(diag, Cx<float>{v.z, v.w}), acc[(sp + 2) * 3 + col]));
+    outr[p * V + s] = make_float4(up.re, up.im, lo.re, lo.im);
+  }
+}
+
+// canonical complex64 [rhs][site][12] <-> S4
+__global__ void pack_s4_kernel(const float2* __restrict__ aos, float4* __restrict__ s4, int V, int nrhs) {
+  const size_t n = (size_t)nrhs * 6 * V;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t site = t % V, q = t / V;
+    const size_t p = q % 6, r = q / 6;
+    const size_t sp = p / 3, col = p % 3;
+    const float2* a = aos + ((size_t)r * V + site) * 12;
+    const float2 u = a[sp * 3 + col], l = a[(sp + 2) * 3 + col];
+    s4[t] = make_float4(u.x, u.y, l.x, l.y);
+  }
+}
+
+__global__ void unpack_s4_kernel(const float4* __restrict__ s4, float2* __restrict__ aos, int V, int nrhs) {
+  const size_t n = (size_t)nrhs * 6 * V;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t site = t % V, q = t / V;
+    const size_t p = q % 6, r = q / 6;
+    const size_t sp = p / 3, col = p % 3;
+    const float4 v = s4[t];
+    float2* a = aos + ((size_t)r * V + site) * 12;
+    a[sp * 3 + col] = make_float2(v.x, v.y);
+    a[(sp + 2) * 3 + col] = make_float2(v.z, v.w);
+  }
+}
+
+// U32 planes (mu*9 + e, site) -> S4 links: 5 float4 (pairs of elements) or 3 (rows 0, 1)
+__global__ void links_s4_kernel(const float2* __restrict__ u32, float4* __restrict__ l5, float4* __restrict__ l3,
+                                int V) {
+  const size_t n = (size_t)4 * V;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t site = t % V, mu = t / V;
+    float2 e[10];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) e[k] = u32[(mu * 9 + k) * V + site];
+    e[9] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) l5[(mu * 5 + k) * V + site] = make_float4(e[2 * k].x, e[2 * k].y, e[2 * k + 1].x, e[2 * k + 1].y);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) l3[(mu * 3 + k) * V + site] = make_float4(e[2 * k].x, e[2 * k].y, e[2 * k + 1].x, e[2 * k + 1].y);
+  }
+}
+
+int cap_grid32(size_t n) {
+  size_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)(b > 0 ? b : 1);
+}
+
+}  // namespace
+
+int launch_pack_s4(ov_ctx* ctx, const float2* aos, float4* s4, int nrhs, cudaStream_t s) {
+  pack_s4_kernel<<<cap_grid32((size_t)nrhs * 6 * ctx->g.V), 256, 0, s>>>(aos, s4, ctx->g.V, nrhs);
+  OV_CHECK_LAUNCH(ctx, "pack_s4_kernel");
+  return OV_OK;
+}
+
+int launch_unpack_s4(ov_ctx* ctx, const float4* s4, float2* aos, int nrhs, cudaStream_t s) {
+  unpack_s4_kernel<<<cap_grid32((size_t)nrhs * 6 * ctx->g.V), 256, 0, s>>>(s4, aos, ctx->g.V, nrhs);
+  OV_CHECK_LAUNCH(ctx, "unpack_s4_kernel");
+  return OV_OK;
+}
+
+// out = H_W in on the S4 layout; comp selects the 3-float4 (compressed) links.
+int launch_hw32_s4(ov_ctx* ctx, const float4* in, float4* out, int nrhs, int comp, cudaStream_t s) {
+  int st = OV_OK;
+  float4* l5 = (float4*)ws_get(ctx, "gauge.s4l5", sizeof(float4) * 4 * 5 * (size_t)ctx->g.V, &st);
+  float4* l3 = (float4*)ws_get(ctx, "gauge.s4l3", sizeof(float4) * 4 * 3 * (size_t)ctx->g.V, &st);
+  if (st != OV_OK) return st;
+  if (!ctx->have_s4) {
+    links_s4_kernel<<<cap_grid32((size_t)4 * ctx->g.V), 256, 0, s>>>(ctx->U32, l5, l3, ctx->g.V);
+    ctx->have_s4 = true;
+  }
+  constexpr int NT = 128;
+  dim3 grid((ctx->g.V + NT - 1) / NT, nrhs);
+  const float diag = (float)(4.0 - ctx->m0);
+  cudaEvent_t ev;
+  kt_begin(ctx, KC_DSLASH, s, &ev);
+  if (comp)
+    hw32_s4_kernel<true, NT><<<grid, NT, 0, s>>>(in, out, l3, ctx->g, diag);
+  else
+    hw32_s4_kernel<false, NT><<<grid, NT, 0, s>>>(in, out, l5, ctx->g, diag);
+  kt_end(ctx, KC_DSLASH, s, ev);
+  OV_CHECK_LAUNCH(ctx, "hw32_s4_kernel");
+  return OV_OK;
+}

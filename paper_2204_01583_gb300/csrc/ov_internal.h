@@ -80,6 +80,7 @@ struct ov_ctx {
   bool have_gauge = false;
   bool have_c32 = false;               // compressed FP32 links (workspace "gauge.c32") are current
   bool have_b32 = false;               // broadcast FP32 links for the paired layout ("gauge.b32")
+  bool have_s4 = false;                // FP32 links for the spin-paired float4 layout
   std::map<int, int> hw32_choice;      // nrhs -> autotuned FP32 stencil variant
   int hw32_force = -1;                 // ov_set_hw32_variant
   bool no_coop = true;                 // ov_set_persistent(ctx, 1) enables the persistent loop
@@ -140,6 +141,10 @@ int launch_hw32_tuned(ov_ctx* ctx, const float2* in, float2* out, int nrhs, cuda
 int hw32_variant_count();  // SoA variants; index hw32_variant_count() is the paired kernel
 void hw32_variant_info(int k, int* rt, int* comp, int* nt);
 float hw32_time_soa_variants(ov_ctx* ctx, const float2* in, float2* out, int nrhs, cudaStream_t s, int* best);
+// spin-paired float4 FP32 layout (dslash32.cu)
+int launch_pack_s4(ov_ctx* ctx, const float2* aos, float4* s4, int nrhs, cudaStream_t s);
+int launch_unpack_s4(ov_ctx* ctx, const float4* s4, float2* aos, int nrhs, cudaStream_t s);
+int launch_hw32_s4(ov_ctx* ctx, const float4* in, float4* out, int nrhs, int comp, cudaStream_t s);
 // paired FP32 layout (pair32.cu)
 const float4* pair_links(ov_ctx* ctx, cudaStream_t s, int* st);
 int launch_pack_pair32(ov_ctx* ctx, const float2* aos, float4* pr, int nrhs, cudaStream_t s);
