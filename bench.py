@@ -59,6 +59,9 @@ WORKLOADS = {
     # stencil only: H_W on 12 right-hand sides (diagnostic of the HBM roofline)
     "dslash-16^3x32-fp32-12rhs": dict(dims=(16, 16, 16, 32), eps=0.6, nsrc=12, kind="dslash", prec="fp32"),
     "dslash-16^3x32-fp64-12rhs": dict(dims=(16, 16, 16, 32), eps=0.6, nsrc=12, kind="dslash", prec="fp64"),
+    # sigma vs nodes per contour with the paper's two-ellipse contour (rescaled), 8^4
+    "sigma-8^4-paper-contour": dict(dims=(8, 8, 8, 8), eps=0.5, nsrc=4, src="gauss", kind="sigma",
+                                    n_list=(100, 250, 500, 1000)),
 }
 DEFAULT_WORKLOAD = "8^4-fp64-nq64-4src"
 M0 = 1.6
@@ -549,11 +552,63 @@ def run_dslash(args, wl):
     return 0
 
 
+def run_sigma(args, wl):
+    """sigma = |s's - b'b| / b'b and device time per source apply versus the nodes per
+    contour, with the paper's contour form (alpha 0.1, rho 1.1999, centres +-1.2) scaled by
+    the Lanczos bound of |lambda|; FP64 coefficient-space solve, tol 1e-13."""
+    import torch
+
+    from paper_2204_01583_gb300 import build as build_lib
+
+    build_lib()
+    from paper_2204_01583_gb300 import lib
+
+    dims = wl["dims"]
+    U, b = workload_inputs(wl, 0)
+    ctx = lib.Context(dims, bc_t=-1, m0=M0)
+    ctx.set_gauge(torch.from_numpy(U).cuda())
+    spec = ctx.place_contour(16, steps=150)
+    scale = spec["abs_max_bound"] / 2.35
+    bd = torch.from_numpy(b).cuda()
+    out = torch.empty_like(bd)
+    nsrc = b.shape[0]
+    rows = []
+    for n in wl["n_list"]:
+        ctx.set_contour_ellipse(n, 1.2 * scale, 1.1999 * scale, 0.1, lib.OV_CONTOUR_PAIR)
+        o = ctx.opts(mode="fp64_2pass", tol=1e-13)
+        for _ in range(args.warmup):
+            ctx.sgn(bd, out, nsrc, o)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            st = ctx.sgn(bd, out, nsrc, o)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        s = out.reshape(nsrc, -1)
+        bb = bd.reshape(nsrc, -1)
+        sig = ((s.abs() ** 2).sum(1) - (bb.abs() ** 2).sum(1)).abs() / (bb.abs() ** 2).sum(1)
+        rows.append({"nodes_per_contour": n, "total_nodes": 2 * n, "sigma_max": float(sig.max()),
+                     "sigma_mean": float(sig.mean()), "ms_per_apply": ms / nsrc, "iterations": st["iterations"]})
+    line = {"metric": "sigma vs N_q (paper contour form)", "value": rows[-1]["sigma_max"], "unit": "sigma",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "lattice": "x".join(map(str, dims)), "link_eps": wl["eps"],
+                       "sources": nsrc, "contour": "alpha 0.1, rho 1.1999 s, centres +-1.2 s, s = bound/2.35",
+                       "scale": scale, "spectrum": spec},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     wl = WORKLOADS[args.workload]
     if wl.get("kind") == "dslash":
         return run_dslash(args, wl)
+    if wl.get("kind") == "sigma":
+        return run_sigma(args, wl)
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_ours(args, wl)
