@@ -324,13 +324,13 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
   const double inv_n = 1.0 / S->n_cur;
   const double alpha = S->alpha;
   const int na = a.prm->vec_shifts ? S->n_act : 0;
-  const size_t e = (size_t)blockIdx.x * NT2 + threadIdx.x;
   double nrm = 0.0;
-  if (e < n12) {
+  // grid-stride: a few blocks per source (fewer partials and atomics than one block per chunk)
+  for (size_t e = (size_t)blockIdx.x * NT2 + threadIdx.x; e < n12; e += (size_t)gridDim.x * NT2) {
     const Cx<R> v = lz_v<R>(ld<R>(Ui + e), (R)inv_n);
     const Cx<R> u = lz_next<R>(ld<R>(W + e), v, (R)alpha);
     st<R>(W + e, u);
-    nrm = (double)u.re * (double)u.re + (double)u.im * (double)u.im;
+    nrm += (double)u.re * (double)u.re + (double)u.im * (double)u.im;
     double sre = 0.0, sim = 0.0;
     const int* idx = a.act_idx + (size_t)r * ns;
     const double2* al = a.act_l + (size_t)r * ns;
@@ -800,7 +800,7 @@ namespace {
 template <typename R>
 struct SolveWs {
   SolveArgs<R> a{};
-  int nblk1 = 0, nblk2 = 0;
+  int nblk1 = 0, nblk2 = 0, nblk2u = 0;
   int nslots = 3;
   SolveParams* prm_dev = nullptr;
 };
@@ -814,7 +814,10 @@ int setup_ws(ov_ctx* ctx, int nsrc, int ns, bool want_x, bool want_sacc, bool wa
   int st = OV_OK;
   std::string t(tag);
   w->nblk1 = (V + kSplitSites - 1) / kSplitSites;
+  // K2 runs grid-stride with about two blocks per SM in total (at least 8 per source);
+  // the init kernel uses the same partial buffer with up to ceil(12V / NT2) blocks
   w->nblk2 = (int)((n12 + NT2 - 1) / NT2);
+  w->nblk2u = (int)std::min<size_t>(w->nblk2, std::max<size_t>(8, (size_t)(2 * 152) / (size_t)nsrc));
   auto& a = w->a;
   w->nslots = nslots;
   a.ring = (T*)ws_get(ctx, (t + ".ring").c_str(), sizeof(T) * (size_t)nslots * n12 * nsrc, &st);
@@ -861,7 +864,7 @@ int launch_iteration(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, cudaStream_t s)
   lanczos_hw_kernel<R><<<dim3(w.nblk1, nsrc), NT1, 0, s>>>(w.a);
   kt_end(ctx, KC_LANCZOS_HW, s, ev);
   kt_begin(ctx, KC_SHIFT_UPDATE, s, &ev);
-  lanczos_update_kernel<R><<<dim3(w.nblk2, nsrc), NT2, 0, s>>>(w.a);
+  lanczos_update_kernel<R><<<dim3(w.nblk2u, nsrc), NT2, 0, s>>>(w.a);
   kt_end(ctx, KC_SHIFT_UPDATE, s, ev);
   return OV_OK;
 }
@@ -886,7 +889,7 @@ int run_iterations(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, int nshift, int f
       if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaStreamBeginCapture");
       for (int k = 0; k < chunk; ++k) {
         lanczos_hw_kernel<R><<<dim3(w.nblk1, nsrc), NT1, 0, ctx->cap_stream>>>(w.a);
-        lanczos_update_kernel<R><<<dim3(w.nblk2, nsrc), NT2, 0, ctx->cap_stream>>>(w.a);
+        lanczos_update_kernel<R><<<dim3(w.nblk2u, nsrc), NT2, 0, ctx->cap_stream>>>(w.a);
       }
       cudaGraph_t gph = nullptr;
       e = cudaStreamEndCapture(ctx->cap_stream, &gph);
@@ -1514,7 +1517,7 @@ int lanczos_tridiag(ov_ctx* ctx, int steps, int squared, std::vector<double>& al
       a.stencil = tmp2;
     }
     lanczos_hw_kernel<double><<<dim3(w.nblk1, 1), NT1, 0, s>>>(a);
-    lanczos_update_kernel<double><<<dim3(w.nblk2, 1), NT2, 0, s>>>(a);
+    lanczos_update_kernel<double><<<dim3(w.nblk2u, 1), NT2, 0, s>>>(a);
   }
   OV_CHECK_LAUNCH(ctx, "lanczos bound kernels");
   SrcState S;
