@@ -64,6 +64,8 @@ WORKLOADS = {
                                     n_list=(100, 250, 500, 1000)),
 }
 DEFAULT_WORKLOAD = "8^4-fp64-nq64-4src"
+# arithmetic type of the vector work per solver mode (scalars, inner products and the sum stay f64)
+DTYPES = {"fp64": "f64", "fp64_2pass": "f64", "fp64_regen": "f64", "mixed": "f32+f64", "f32x2": "f32x2"}
 M0 = 1.6
 
 
@@ -74,7 +76,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default=None, choices=[None, "fp64", "fp64_2pass", "fp64_regen", "mixed"])
+    ap.add_argument("--mode", default=None, choices=[None, "fp64", "fp64_2pass", "fp64_regen", "mixed", "f32x2"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variant", type=int, default=None, help="dslash workloads: time only this FP32 stencil variant")
@@ -361,15 +363,15 @@ def run_ours(args, wl):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if mode == "mixed" else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPES[mode], "data": "synthetic",
         "config": config_dict(args, wl, mode), "clocks": clocks, "e2e": e2e,
         "gpu_launches": int(sum(s["launches"] for s in stats)), "roofline": roof, "kernels": kernels,
         "solver": {"iterations": stats[-1]["iterations"], "max_residual": stats[-1]["max_residual"],
                    "error_bound": stats[-1]["error_bound"], "converged": stats[-1]["converged"],
                    "spectrum": spec},
     }
-    if mode == "mixed" and args.compare_steps > 0:
-        line["mixed_vs_fp64"] = compare_fp64(ctx, wl, bd, out, nsrc, stream, flush, args.compare_steps,
+    if mode in ("mixed", "f32x2") and args.compare_steps > 0:
+        line[f"{mode}_vs_fp64"] = compare_fp64(ctx, wl, bd, out, nsrc, stream, flush, args.compare_steps,
                                              total_ms / args.steps)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         z, c, c0 = ctx.get_contour()
@@ -411,7 +413,7 @@ def compare_fp64(ctx, wl, bd, out_mixed, nsrc, stream, flush, steps, mixed_ms):
     the largest relative difference per source between the mixed and FP64 results."""
     import torch
 
-    res = {"mixed_ms_per_step": mixed_ms}
+    res = {"ms_per_step": mixed_ms}
     ref = None
     for mode in ("fp64", "fp64_2pass"):
         o = ctx.opts(mode=mode, tol=wl["tol"])

@@ -82,7 +82,15 @@ typedef enum {
   OV_MODE_FP64_2PASS = 2,
   /* As OV_MODE_FP64_2PASS, always regenerating the basis (memory: three vectors per
    * source). */
-  OV_MODE_FP64_REGEN = 3
+  OV_MODE_FP64_REGEN = 3,
+  /* As OV_MODE_FP64_2PASS with every vector operation -- the H_W stencil, the Lanczos
+   * updates and the stored basis -- in FP32-pair (double-float) arithmetic on the FP32
+   * units: each real is an unevaluated sum of two floats (~48-bit significand), sums
+   * by error-free two-sum, products by FMA-based exact products.  Recurrence scalars,
+   * inner products and the quadrature sum stay FP64.  All sources run in the same
+   * launches.  Accuracy ~1e-13 relative; on GB300 (FP64 at 1/58 of the FP32 rate) it
+   * replaces FP64 arithmetic in the bulk. */
+  OV_MODE_F32X2 = 4
 } ov_mode;
 
 typedef enum {

@@ -132,7 +132,7 @@ int check_opts(ov_ctx* ctx, const ov_solve_opts& o) {
   if (!(o.tol > 0.0) || !(o.tol < 1.0)) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "tol must be in (0, 1)");
   if (o.max_iter < 1) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "max_iter must be >= 1");
   if (o.mode != OV_MODE_FP64 && o.mode != OV_MODE_MIXED && o.mode != OV_MODE_FP64_2PASS &&
-      o.mode != OV_MODE_FP64_REGEN)
+      o.mode != OV_MODE_FP64_REGEN && o.mode != OV_MODE_F32X2)
     return ctx_fail(ctx, OV_ERR_INVALID_ARG, "unknown solver mode");
   return OV_OK;
 }
@@ -164,7 +164,7 @@ int sign_core(ov_ctx* ctx, const double2* b_dev, int nrhs, const ov_solve_opts& 
   if (st != OV_OK) return st;
   if (o.mode == OV_MODE_FP64 || xs) {
     st = solve_sign_soa(ctx, b_soa, s_soa, nrhs, o, so, s, xs);
-  } else if (o.mode == OV_MODE_FP64_2PASS || o.mode == OV_MODE_FP64_REGEN) {
+  } else if (o.mode == OV_MODE_FP64_2PASS || o.mode == OV_MODE_FP64_REGEN || o.mode == OV_MODE_F32X2) {
     st = solve_sign_2pass(ctx, b_soa, s_soa, nrhs, o, so, s);
   } else if (o.mode == OV_MODE_MIXED) {
     st = solve_sign_mixed(ctx, b_soa, s_soa, nrhs, o, so, s);
@@ -285,6 +285,7 @@ int ov_set_gauge(ov_ctx* ctx, const double* U, int on_device, void* stream) {
   ctx->have_c32 = false;
   ctx->have_b32 = false;
   ctx->have_s4 = false;
+  ctx->have_df = false;
   return OV_OK;
 }
 

@@ -4,31 +4,104 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "ov_internal.h"
+
+// ---------------------------------------------------------- double-float reals
+// DF: a real carried as an unevaluated sum hi + lo of two FP32 numbers (|lo| <= ulp(hi)/2
+// after each operation), giving ~48-bit significands from FP32 instructions alone.
+// Sums use Knuth's error-free two-sum, products the FMA-based exact product; every
+// operation renormalises with a fast two-sum.  On GB300, where FP64 runs at 1/58 of the
+// FP32 rate, this carries FP64-class accuracy at FP32 throughput.
+struct DF {
+  float hi, lo;
+  __host__ __device__ __forceinline__ DF() {}
+  __host__ __device__ __forceinline__ DF(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ explicit DF(double x) {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(x - (double)hi);
+  }
+  __device__ __forceinline__ explicit DF(int x) : hi((float)x), lo(0.f) {}
+  __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ DF df_quick_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return DF(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ DF operator-(DF a) { return DF(-a.hi, -a.lo); }
+__device__ __forceinline__ DF operator+(DF a, DF b) {
+  float s, e;
+  df_two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return df_quick_two_sum(s, e);
+}
+__device__ __forceinline__ DF operator-(DF a, DF b) { return a + (-b); }
+__device__ __forceinline__ DF operator*(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_quick_two_sum(p, e);
+}
+// a * b + c with one renormalisation
+__device__ __forceinline__ DF fma(DF a, DF b, DF c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float pe = __fmaf_rn(a.hi, b.hi, -p);
+  float s, e;
+  df_two_sum(c.hi, p, s, e);
+  float t = __fadd_rn(__fadd_rn(e, pe), c.lo);
+  t = __fmaf_rn(a.hi, b.lo, t);
+  t = __fmaf_rn(a.lo, b.hi, t);
+  return df_quick_two_sum(s, t);
+}
+__device__ __forceinline__ DF& operator+=(DF& a, DF b) { return a = a + b; }
+__device__ __forceinline__ DF& operator-=(DF& a, DF b) { return a = a - b; }
 
 template <typename R>
 struct Cx {
   R re, im;
 };
 
+// Storage type of one complex number and its (un)packing, per arithmetic type.
 template <typename R> struct Store;
-template <> struct Store<double> { using T = double2; };
-template <> struct Store<float> { using T = float2; };
+template <> struct Store<double> {
+  using T = double2;
+  __device__ __forceinline__ static Cx<double> unpack(double2 v) { return {v.x, v.y}; }
+  __device__ __forceinline__ static double2 pack(Cx<double> c) { return make_double2(c.re, c.im); }
+};
+template <> struct Store<float> {
+  using T = float2;
+  __device__ __forceinline__ static Cx<float> unpack(float2 v) { return {v.x, v.y}; }
+  __device__ __forceinline__ static float2 pack(Cx<float> c) { return make_float2(c.re, c.im); }
+};
+template <> struct Store<DF> {
+  using T = float4;  // (re.hi, re.lo, im.hi, im.lo)
+  __device__ __forceinline__ static Cx<DF> unpack(float4 v) { return {DF(v.x, v.y), DF(v.z, v.w)}; }
+  __device__ __forceinline__ static float4 pack(Cx<DF> c) { return make_float4(c.re.hi, c.re.lo, c.im.hi, c.im.lo); }
+};
 
 // Loads: CG = false reads through the read-only (non-coherent) path, for data no block
 // writes during the launch; CG = true reads from L2 (ld.global.cg), for data other blocks
 // of a persistent launch wrote before a grid barrier.
 template <typename R, bool CG = false>
 __device__ __forceinline__ Cx<R> ld(const typename Store<R>::T* p) {
-  typename Store<R>::T v = CG ? __ldcg(p) : __ldg(p);
-  return {v.x, v.y};
+  return Store<R>::unpack(CG ? __ldcg(p) : __ldg(p));
 }
 template <typename R>
 __device__ __forceinline__ void st(typename Store<R>::T* p, Cx<R> v) {
-  typename Store<R>::T w;
-  w.x = v.re;
-  w.y = v.im;
-  *p = w;
+  *p = Store<R>::pack(v);
+}
+// complex from two doubles in the storage precision (exact split for DF)
+template <typename R>
+__device__ __forceinline__ Cx<R> cx_from(double re, double im) {
+  return {(R)re, (R)im};
 }
 
 template <typename R> __device__ __forceinline__ Cx<R> cadd(Cx<R> a, Cx<R> b) { return {a.re + b.re, a.im + b.im}; }
@@ -216,10 +289,94 @@ __device__ __forceinline__ double sum_partials(const double* p, int n, double* s
 constexpr int kSplitNT = 128;
 constexpr int kSplitSites = 32;
 
+// Unit phase: i^q a (q taken mod 4), by swaps and sign flips.
+template <typename R>
+__device__ __forceinline__ Cx<R> uphase(Cx<R> a, int q) {
+  const Cx<R> t = (q & 1) ? Cx<R>{-a.im, a.re} : a;
+  return (q & 2) ? Cx<R>{-t.re, -t.im} : t;
+}
+
+// Phase 1 with one instruction stream for all directions and both hops: mu and the hop
+// are runtime values, A_mu is applied as a permutation and unit phases, and the rows
+// of the link product are a runtime loop that accumulates into shared memory.  Used
+// for double-float arithmetic, where a complex FMA is ~60 FP32 instructions and the
+// unrolled per-direction form (eight hop bodies live in one block) overflows the
+// instruction cache.  Stores the hop sums unscaled (phase 2 applies the -1/2).
+//   A_mu (l0, l1) = (i^qa0 l_{swap}, i^qa1 l_{1-swap}):  A_x = -i sigma_1 (swap, -i, -i),
+//   A_y = -i sigma_2 (swap, -1, +1), A_z = -i sigma_3 (-i, +i), A_t = 1;
+//   A_mu^dag is the transpose with conjugate phases.
+template <typename R, bool CG>
+__device__ __forceinline__ void hw_split_phase1_compact(const typename Store<R>::T* __restrict__ in,
+                                                        const typename Store<R>::T* __restrict__ U, const Geom& g,
+                                                        int site0, Cx<R>* sm) {
+  const int lane = threadIdx.x & 31, mu = threadIdx.x >> 5;
+  const int s = site0 + lane;
+  const int V = g.V;
+  Cx<R>* acc = sm + mu * 12 * kSplitSites + lane;  // component k at acc[k * kSplitSites]
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k * kSplitSites] = {R(0), R(0)};
+  if (s >= V) return;
+  const int Lm = g.L[mu], stm = g.st[mu];
+  const int cm = (s / stm) % Lm;  // coordinate along mu
+  const int bsg = (mu == 3) ? g.bc_t : 1;
+  const bool swap = mu < 2;
+  const int qa0 = (mu == 3) ? 0 : (mu == 1) ? 2 : 3;
+  const int qa1 = (mu == 0) ? 3 : (mu == 2) ? 1 : 0;
+  const int qb0 = (4 - (swap ? qa1 : qa0)) & 3, qb1 = (4 - (swap ? qa0 : qa1)) & 3;
+  const int k2 = swap ? 3 : 2, k3 = swap ? 2 : 3;  // lower spin feeding row 0 / row 1 of A
+#pragma unroll 1
+  for (int dir = 0; dir < 2; ++dir) {
+    const bool wrap = dir == 0 ? (cm + 1 == Lm) : (cm == 0);
+    const int sgn = wrap ? bsg : 1;
+    const int sn = dir == 0 ? (wrap ? s - (Lm - 1) * stm : s + stm) : (wrap ? s + (Lm - 1) * stm : s - stm);
+    const int sl = dir == 0 ? s : sn;  // link site
+    const int qd = dir == 0 ? 2 : 0;   // forward hop: h = psi_up - A psi_lo, lower gets -A^dag u
+    const int qs = sgn < 0 ? 2 : 0;    // boundary sign
+    Cx<R> h0[3], h1[3];
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+      const Cx<R> p0 = ld<R, CG>(in + (0 * 3 + col) * (size_t)V + sn);
+      const Cx<R> p1 = ld<R, CG>(in + (1 * 3 + col) * (size_t)V + sn);
+      const Cx<R> pa = ld<R, CG>(in + (k2 * 3 + col) * (size_t)V + sn);
+      const Cx<R> pb = ld<R, CG>(in + (k3 * 3 + col) * (size_t)V + sn);
+      h0[col] = cadd(p0, uphase(pa, qa0 + qd));
+      h1[col] = cadd(p1, uphase(pb, qa1 + qd));
+    }
+    const typename Store<R>::T* Ul = U + (size_t)mu * 9 * V + sl;
+#pragma unroll 1
+    for (int i = 0; i < 3; ++i) {
+      Cx<R> u0 = {R(0), R(0)}, u1 = {R(0), R(0)};
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        // forward: U[i][j]; backward: (U^dag)[i][j] = conj(U[j][i])
+        const int e = dir == 0 ? (i * 3 + j) : (j * 3 + i);
+        Cx<R> l = ld<R>(Ul + e * (size_t)V);
+        if (dir) l.im = -l.im;
+        u0 = cfma(l, h0[j], u0);
+        u1 = cfma(l, h1[j], u1);
+      }
+      Cx<R>* a = acc + i * kSplitSites;
+      a[0 * 3 * kSplitSites] = cadd(a[0 * 3 * kSplitSites], uphase(u0, qs));
+      a[1 * 3 * kSplitSites] = cadd(a[1 * 3 * kSplitSites], uphase(u1, qs));
+      a[2 * 3 * kSplitSites] = cadd(a[2 * 3 * kSplitSites], uphase(swap ? u1 : u0, qb0 + qd + qs));
+      a[3 * 3 * kSplitSites] = cadd(a[3 * 3 * kSplitSites], uphase(swap ? u0 : u1, qb1 + qd + qs));
+    }
+  }
+}
+
+// exact halving (power-of-two scaling)
+__device__ __forceinline__ DF half_of(DF x) { return DF(0.5f * x.hi, 0.5f * x.lo); }
+template <typename R>
+__device__ __forceinline__ R half_of(R x) { return R(0.5) * x; }
+
 template <typename R, bool CG = false>
 __device__ __forceinline__ void hw_split_phase1(const typename Store<R>::T* __restrict__ in,
                                                 const typename Store<R>::T* __restrict__ U, const Geom& g,
                                                 int site0, Cx<R>* sm) {
+  if constexpr (std::is_same<R, DF>::value) {
+    hw_split_phase1_compact<R, CG>(in, U, g, site0, sm);
+    return;
+  }
   const int lane = threadIdx.x & 31, mu = threadIdx.x >> 5;
   const int s = site0 + lane;
   Cx<R> acc[12];
@@ -254,8 +411,15 @@ __device__ __forceinline__ bool hw_split_phase2(const typename Store<R>::T* __re
   for (int q = 0; q < 3; ++q) {
     const int k = 3 * grp + q;
     Cx<R> v = cscale(diag, ld<R, CG>(in + k * (size_t)g.V + s));
+    if constexpr (std::is_same<R, DF>::value) {  // unscaled hop sums (compact phase 1)
+      Cx<R> t = sm[k * kSplitSites + lane];
 #pragma unroll
-    for (int mu = 0; mu < 4; ++mu) v = cadd(v, sm[(mu * 12 + k) * kSplitSites + lane]);
+      for (int mu = 1; mu < 4; ++mu) t = cadd(t, sm[(mu * 12 + k) * kSplitSites + lane]);
+      v = csub(v, Cx<R>{half_of(t.re), half_of(t.im)});
+    } else {
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) v = cadd(v, sm[(mu * 12 + k) * kSplitSites + lane]);
+    }
     o[q] = (k >= 6) ? cneg(v) : v;
   }
   return true;

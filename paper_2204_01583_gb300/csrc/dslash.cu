@@ -80,6 +80,15 @@ __global__ void __launch_bounds__(kNT) hw_kernel(const typename Store<R>::T* __r
   for (int k = 0; k < 12; ++k) st<R>(out + off + k * (size_t)g.V + s, o[k]);
 }
 
+// FP64 link planes -> double-float planes (hi, lo per real; float4 per complex)
+__global__ void links_df_kernel(const double2* __restrict__ u64, float4* __restrict__ udf, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = u64[t];
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    udf[t] = make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
+  }
+}
+
 int grid_for(size_t n, int nt) {
   size_t b = (n + nt - 1) / nt;
   if (b > 152 * 16) b = 152 * 16;
@@ -162,5 +171,18 @@ int launch_gamma5_aos(ov_ctx* ctx, const double2* in, double2* out, int nrhs, cu
   const size_t n = (size_t)nrhs * ctx->g.V * 12;
   gamma5_aos_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, out, ctx->g.V, nrhs);
   OV_CHECK_LAUNCH(ctx, "gamma5_aos_kernel");
+  return OV_OK;
+}
+
+int ensure_links_df(ov_ctx* ctx, cudaStream_t s) {
+  int st = OV_OK;
+  const size_t n = (size_t)4 * 9 * ctx->g.V;
+  ctx->Udf = (float4*)ws_get(ctx, "gauge.df", sizeof(float4) * n, &st);
+  if (st != OV_OK) return st;
+  if (!ctx->have_df) {
+    links_df_kernel<<<grid_for(n, 256), 256, 0, s>>>(ctx->U64, ctx->Udf, n);
+    OV_CHECK_LAUNCH(ctx, "links_df_kernel");
+    ctx->have_df = true;
+  }
   return OV_OK;
 }

@@ -81,6 +81,8 @@ struct ov_ctx {
   bool have_c32 = false;               // compressed FP32 links (workspace "gauge.c32") are current
   bool have_b32 = false;               // broadcast FP32 links for the paired layout ("gauge.b32")
   bool have_s4 = false;                // FP32 links for the spin-paired float4 layout
+  float4* Udf = nullptr;               // double-float links (workspace "gauge.df") when have_df
+  bool have_df = false;
   std::map<int, int> hw32_choice;      // nrhs -> autotuned FP32 stencil variant
   int hw32_force = -1;                 // ov_set_hw32_variant
   bool no_coop = true;                 // ov_set_persistent(ctx, 1) enables the persistent loop
@@ -141,6 +143,8 @@ int launch_hw32_tuned(ov_ctx* ctx, const float2* in, float2* out, int nrhs, cuda
 int hw32_variant_count();  // SoA variants; index hw32_variant_count() is the paired kernel
 void hw32_variant_info(int k, int* rt, int* comp, int* nt);
 float hw32_time_soa_variants(ov_ctx* ctx, const float2* in, float2* out, int nrhs, cudaStream_t s, int* best);
+// double-float links for the FP32-pair solve (dslash.cu)
+int ensure_links_df(ov_ctx* ctx, cudaStream_t s);
 // spin-paired float4 FP32 layout (dslash32.cu)
 int launch_pack_s4(ov_ctx* ctx, const float2* aos, float4* s4, int nrhs, cudaStream_t s);
 int launch_unpack_s4(ov_ctx* ctx, const float4* s4, float2* aos, int nrhs, cudaStream_t s);
@@ -175,7 +179,8 @@ int solve_nodes_soa(ov_ctx* ctx, const double2* b_soa, int nsrc, int ns, const s
                     const std::vector<double2>& ch, double2 c0, double2* out_soa, double2* xs_soa,
                     const ov_solve_opts& o, SolveOut* so, cudaStream_t s);
 
-// two-pass FP64 variant (OV_MODE_FP64_2PASS)
+// coefficient-space Lanczos (OV_MODE_FP64_2PASS / _REGEN in FP64, OV_MODE_F32X2 in
+// double-float arithmetic)
 int solve_sign_2pass(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nrhs, const ov_solve_opts& o,
                      SolveOut* so, cudaStream_t s);
 

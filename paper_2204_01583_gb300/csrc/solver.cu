@@ -34,6 +34,7 @@
 #include <cstdio>
 #include <string>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include <cooperative_groups.h>
@@ -44,6 +45,11 @@ namespace {
 
 constexpr int NT1 = 128;  // K1: stencil + Lanczos epilogue; K3: regeneration pass
 constexpr int NT2 = 256;  // K2: vector updates
+// Resident blocks per SM the stencil kernels are compiled for: 4 (<= 128 registers) for
+// FP64; 6 (<= 80 registers) for double-float, whose stencil is issue-bound
+// and gains from the extra warps.
+template <typename R>
+constexpr int k1_min_blocks() { return std::is_same<R, DF>::value ? 6 : 4; }
 
 struct SrcState {
   double bnorm;   // ||b||
@@ -58,6 +64,39 @@ struct SrcState {
   double node_updates;  // sum over iterations of n_act
   int k_final;    // second pass: number of Lanczos vectors to regenerate
   int pad_;
+  // derived once per iteration by the block that updates the norms (not per thread):
+  double inv_n;   // 1 / ||U_i||
+  double cm;      // ||U_i|| / ||U_{i-1}|| (0 at i = 1)
+  float df[6];    // inv_n, cm, alpha as double-float (hi, lo) pairs
+  int pad2_;
+};
+
+// exact double-float split of an FP64 value: hi = rn(x), lo = rn(x - hi)
+__device__ __forceinline__ void df_split(double x, float* d) {
+  d[0] = __double2float_rn(x);
+  d[1] = __double2float_rn(x - (double)d[0]);
+}
+
+// inv_n, cm and their double-float forms from n_cur, n_prev and iter
+__device__ __forceinline__ void set_norm_scalars(SrcState* S) {
+  S->inv_n = 1.0 / S->n_cur;
+  S->cm = (S->iter > 1) ? S->n_cur / S->n_prev : 0.0;
+  df_split(S->inv_n, S->df + 0);
+  df_split(S->cm, S->df + 2);
+}
+
+// An FP64 recurrence scalar in the vector arithmetic type; for double-float, from its
+// stored split (no per-thread FP64 conversion).
+template <typename R>
+__device__ __forceinline__ R scal(double v, const float*) { return (R)v; }
+template <>
+__device__ __forceinline__ DF scal<DF>(double, const float* d) { return DF(d[0], d[1]); }
+
+// Per-iteration scalars of the regeneration pass, in the vector arithmetic type.
+template <typename R>
+struct RegenRec {
+  R inv_n, cm, alpha, pad;
+  Cx<R> g;
 };
 
 struct ShiftState {
@@ -84,6 +123,7 @@ struct SolveArgs {
   T* p;               // [src][nshift][12V]
   T* x;               // [src][nshift][12V] or null
   double2* sacc;      // [src][12V] weighted sum (FP64) or null
+  T* ssum;            // [src][12V] regeneration-pass sum in the vector type (double-float) or null
   const T* stencil;   // optional pre-applied H U_i for K1 ([src][12V]) or null
   SrcState* src;
   ShiftState* sh;     // [src][nshift]
@@ -100,6 +140,7 @@ struct SolveArgs {
   double* hist_a;     // [src][max_iter] or null
   double* hist_b;
   const double2* gco; // [src][max_iter] second-pass coefficients or null
+  const RegenRec<R>* rrec;  // [src][max_iter] regeneration-pass scalars or null
   const double* tol_src;  // [src] per-source tolerance or null (then SolveParams::tol)
   const SolveParams* prm;
   const T* U;         // links
@@ -124,6 +165,8 @@ __device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a,
 __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ DF rmul(DF a, DF b) { return a * b; }
+__device__ __forceinline__ DF rfma(DF a, DF b, DF c) { return fma(a, b, c); }
 
 // w = (H U_i) / n_i - (n_i / n_{i-1}) U_{i-1}   (second term absent at i = 1)
 template <typename R>
@@ -145,6 +188,70 @@ template <typename R>
 __device__ __forceinline__ Cx<R> lz_next(Cx<R> w, Cx<R> v, R alpha) {
   return {rfma(-alpha, v.re, w.re), rfma(-alpha, v.im, w.im)};
 }
+
+// Per-thread partial of an inner product.  FP64 and FP32 vectors: an FP64 sum.
+// Double-float vectors: a double-float sum (FP32 instructions only), converted to FP64
+// once per thread -- per-element FP64 conversions would put the kernel on the FP64 pipe.
+template <typename R>
+struct Acc {
+  using T = double;
+  __device__ __forceinline__ static T zero() { return 0.0; }
+  __device__ __forceinline__ static T dot(T acc, Cx<R> u, Cx<R> w) {
+    return acc + ((double)u.re * (double)w.re + (double)u.im * (double)w.im);
+  }
+  __device__ __forceinline__ static double get(T acc) { return acc; }
+  template <int NT>
+  __device__ __forceinline__ static double total(T acc, double* sh) { return block_sum<NT>(acc, sh); }
+};
+template <>
+struct Acc<DF> {
+  using T = DF;
+  __device__ __forceinline__ static T zero() { return DF(0.f, 0.f); }
+  __device__ __forceinline__ static T dot(T acc, Cx<DF> u, Cx<DF> w) {
+    return fma(u.im, w.im, fma(u.re, w.re, acc));
+  }
+  __device__ __forceinline__ static double get(T acc) { return (double)acc; }
+  // block sum in double-float (fixed tree), one FP64 conversion per block; sh >= NT/32 doubles
+  template <int NT>
+  __device__ __forceinline__ static double total(T v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      v = v + DF(__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o));
+    DF* shd = reinterpret_cast<DF*>(sh);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) shd[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+      DF u = shd[0];
+#pragma unroll
+      for (int k = 1; k < NT / 32; ++k) u = u + shd[k];
+      t = (double)u;
+    }
+    __syncthreads();
+    return t;  // valid in thread 0
+  }
+};
+
+// s += g v in the regeneration pass.  FP64 and FP32 vectors: into the FP64 sum.
+// Double-float vectors: into a double-float sum (a.ssum), folded into the FP64 sum
+// after the last iteration.  The element is read and written by this thread only.
+template <typename R>
+struct SumAdd {
+  __device__ __forceinline__ static void add(const SolveArgs<R>& a, size_t idx, Cx<R> g, Cx<R> v) {
+    double2 sv = a.sacc[idx];
+    sv.x += (double)g.re * (double)v.re - (double)g.im * (double)v.im;
+    sv.y += (double)g.re * (double)v.im + (double)g.im * (double)v.re;
+    a.sacc[idx] = sv;
+  }
+};
+template <>
+struct SumAdd<DF> {
+  __device__ __forceinline__ static void add(const SolveArgs<DF>& a, size_t idx, Cx<DF> g, Cx<DF> v) {
+    const Cx<DF> sv = Store<DF>::unpack(a.ssum[idx]);
+    a.ssum[idx] = Store<DF>::pack(cfma(g, v, sv));
+  }
+};
 
 __device__ void mark_done(SrcState* S, int* done_count, int status) {
   S->done = 1;
@@ -176,7 +283,7 @@ __device__ __forceinline__ int block_rank(bool flag, int* total, int* wsh) {
 // The stencil runs 4 threads per site (hw_split_*): a block covers 32 sites.
 // 4 blocks per SM (<= 128 registers): an 8^4 x 4-source grid (512 blocks) fits one wave
 template <typename R>
-__global__ void __launch_bounds__(NT1, 4) lanczos_hw_kernel(SolveArgs<R> a) {
+__global__ void __launch_bounds__(NT1, k1_min_blocks<R>()) lanczos_hw_kernel(SolveArgs<R> a) {
   using T = typename Store<R>::T;
   __shared__ double sh[NT1 / 32];
   __shared__ int wsh[NT1 / 32];
@@ -193,10 +300,10 @@ __global__ void __launch_bounds__(NT1, 4) lanczos_hw_kernel(SolveArgs<R> a) {
   const T* Ui = base + lz_slot(a.prm, i) * n12;
   const T* Um = base + (a.prm->store ? (size_t)(i - 1) : (size_t)((i + 2) % 3)) * n12;  // U_{i-1}
   T* W = base + lz_slot(a.prm, i + 1) * n12;
-  const double inv_n = 1.0 / S->n_cur;
-  const double cm = (i > 1) ? S->n_cur / S->n_prev : 0.0;
+  const double inv_n = S->inv_n;
+  const R inv_nR = scal<R>(inv_n, S->df + 0), cmR = scal<R>(S->cm, S->df + 2);
   const int site0 = blockIdx.x * kSplitSites;
-  double dot = 0.0;
+  typename Acc<R>::T dot = Acc<R>::zero();
   if (a.stencil) {
     // pre-applied operator (H^2 Lanczos for the spectral gap): one thread per (site, 3 components)
     const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5, s = site0 + lane;
@@ -207,9 +314,9 @@ __global__ void __launch_bounds__(NT1, 4) lanczos_hw_kernel(SolveArgs<R> a) {
         const size_t e = (3 * grp + q) * (size_t)V + s;
         const Cx<R> u = ld<R>(Ui + e);
         const Cx<R> um = (i > 1) ? ld<R>(Um + e) : Cx<R>{R(0), R(0)};
-        const Cx<R> w = lz_w<R>(ld<R>(Hs + e), um, (R)inv_n, (R)cm, i == 1);
+        const Cx<R> w = lz_w<R>(ld<R>(Hs + e), um, inv_nR, cmR, i == 1);
         st<R>(W + e, w);
-        dot += (double)u.re * (double)w.re + (double)u.im * (double)w.im;
+        dot = Acc<R>::dot(dot, u, w);
       }
     }
   } else {
@@ -223,13 +330,13 @@ __global__ void __launch_bounds__(NT1, 4) lanczos_hw_kernel(SolveArgs<R> a) {
         const size_t e = (k0 + q) * (size_t)V + s;
         const Cx<R> u = ld<R>(Ui + e);
         const Cx<R> um = (i > 1) ? ld<R>(Um + e) : Cx<R>{R(0), R(0)};
-        const Cx<R> w = lz_w<R>(o[q], um, (R)inv_n, (R)cm, i == 1);
+        const Cx<R> w = lz_w<R>(o[q], um, inv_nR, cmR, i == 1);
         st<R>(W + e, w);
-        dot += (double)u.re * (double)w.re + (double)u.im * (double)w.im;
+        dot = Acc<R>::dot(dot, u, w);
       }
     }
   }
-  double bs = block_sum<NT1>(dot, sh);
+  double bs = Acc<R>::template total<NT1>(dot, sh);
   if (threadIdx.x == 0) {
     a.part1[(size_t)r * gridDim.x + blockIdx.x] = bs;
     __threadfence();
@@ -243,6 +350,7 @@ __global__ void __launch_bounds__(NT1, 4) lanczos_hw_kernel(SolveArgs<R> a) {
     a.cnt[2 * r] = 0;
     const double alpha = tot * inv_n;
     S->alpha = alpha;
+    df_split(alpha, S->df + 4);
     alpha_sh = alpha;
     if (a.hist_a) a.hist_a[(size_t)r * a.prm->max_iter + (i - 1)] = alpha;
     if (!isfinite(alpha)) {
@@ -321,16 +429,15 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
   T* base = a.ring + (size_t)r * a.prm->nslots * n12;
   const T* Ui = base + lz_slot(a.prm, i) * n12;
   T* W = base + lz_slot(a.prm, i + 1) * n12;
-  const double inv_n = 1.0 / S->n_cur;
-  const double alpha = S->alpha;
   const int na = a.prm->vec_shifts ? S->n_act : 0;
-  double nrm = 0.0;
+  const R inv_nR = scal<R>(S->inv_n, S->df + 0), alphaR = scal<R>(S->alpha, S->df + 4);
+  typename Acc<R>::T nrm = Acc<R>::zero();
   // grid-stride: a few blocks per source (fewer partials and atomics than one block per chunk)
   for (size_t e = (size_t)blockIdx.x * NT2 + threadIdx.x; e < n12; e += (size_t)gridDim.x * NT2) {
-    const Cx<R> v = lz_v<R>(ld<R>(Ui + e), (R)inv_n);
-    const Cx<R> u = lz_next<R>(ld<R>(W + e), v, (R)alpha);
+    const Cx<R> v = lz_v<R>(ld<R>(Ui + e), inv_nR);
+    const Cx<R> u = lz_next<R>(ld<R>(W + e), v, alphaR);
     st<R>(W + e, u);
-    nrm += (double)u.re * (double)u.re + (double)u.im * (double)u.im;
+    nrm = Acc<R>::dot(nrm, u, u);
     double sre = 0.0, sim = 0.0;
     const int* idx = a.act_idx + (size_t)r * ns;
     const double2* al = a.act_l + (size_t)r * ns;
@@ -367,7 +474,7 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
       *Sx = sv;
     }
   }
-  double bs = block_sum<NT2>(nrm, sh);
+  double bs = Acc<R>::template total<NT2>(nrm, sh);
   if (threadIdx.x == 0) {
     a.part2[(size_t)r * gridDim.x + blockIdx.x] = bs;
     __threadfence();
@@ -412,6 +519,7 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
   S->n_prev = S->n_cur;
   S->n_cur = beta;
   S->iter = i + 1;
+  set_norm_scalars(S);
   if (beta == 0.0) {
     mark_done(S, a.done_count, OV_OK);
   } else if (ns > 0 && still == 0) {
@@ -425,7 +533,7 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
 // alpha_i and ||U_i|| with the first pass's arithmetic, and add g_i v_i to the sum.
 // One kernel per iteration; the last block advances the iteration counter.
 template <typename R>
-__global__ void __launch_bounds__(NT1, 4) lanczos_regen_kernel(SolveArgs<R> a) {
+__global__ void __launch_bounds__(NT1, k1_min_blocks<R>()) lanczos_regen_kernel(SolveArgs<R> a) {
   using T = typename Store<R>::T;
   __shared__ bool last;
   __shared__ Cx<R> sm[4 * 12 * kSplitSites];
@@ -440,31 +548,23 @@ __global__ void __launch_bounds__(NT1, 4) lanczos_regen_kernel(SolveArgs<R> a) {
   const T* Ui = base + (size_t)(i % 3) * n12;
   const T* Um = base + (size_t)((i + 2) % 3) * n12;
   T* W = base + (size_t)((i + 1) % 3) * n12;
-  const double n_i = (i == 1) ? S->bnorm : a.hist_b[(size_t)r * mi + i - 2];
-  const double n_m = (i <= 2) ? S->bnorm : a.hist_b[(size_t)r * mi + i - 3];
-  const double inv_n = 1.0 / n_i;
-  const double cm = (i > 1) ? n_i / n_m : 0.0;
-  const double alpha = a.hist_a[(size_t)r * mi + i - 1];
-  const double2 g = a.gco[(size_t)r * mi + i - 1];
+  const RegenRec<R> rc = a.rrec[(size_t)r * mi + i - 1];
+  const R inv_nR = rc.inv_n, cmR = rc.cm, alphaR = rc.alpha;
   const int site0 = blockIdx.x * kSplitSites;
   hw_split_phase1<R>(Ui, a.U, a.g, site0, sm);
   __syncthreads();
   Cx<R> o[3];
   int s, k0;
   if (hw_split_phase2<R>(Ui, a.g, site0, a.diag, sm, o, &s, &k0)) {
-    double2* Sx = a.sacc + (size_t)r * n12 + s;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const int k = k0 + q;
       const size_t e = k * (size_t)V + s;
       const Cx<R> um = (i > 1) ? ld<R>(Um + e) : Cx<R>{R(0), R(0)};
-      const Cx<R> w = lz_w<R>(o[q], um, (R)inv_n, (R)cm, i == 1);
-      const Cx<R> v = lz_v<R>(ld<R>(Ui + e), (R)inv_n);
-      st<R>(W + e, lz_next<R>(w, v, (R)alpha));
-      double2 sv = Sx[k * (size_t)V];
-      sv.x += g.x * (double)v.re - g.y * (double)v.im;
-      sv.y += g.x * (double)v.im + g.y * (double)v.re;
-      Sx[k * (size_t)V] = sv;
+      const Cx<R> w = lz_w<R>(o[q], um, inv_nR, cmR, i == 1);
+      const Cx<R> v = lz_v<R>(ld<R>(Ui + e), inv_nR);
+      st<R>(W + e, lz_next<R>(w, v, alphaR));
+      SumAdd<R>::add(a, (size_t)r * n12 + e, rc.g, v);
     }
   }
   __syncthreads();
@@ -527,23 +627,24 @@ __global__ void __launch_bounds__(NT1, 4) lanczos_coop_kernel(SolveArgs<R> a, in
         T* W = (T*)base + lz_slot(a.prm, i + 1) * n12;
         const double inv_n = 1.0 / s_ncur[r];
         const double cm = (i > 1) ? s_ncur[r] / s_nprev[r] : 0.0;
+        const R inv_nR = (R)inv_n, cmR = (R)cm;
         hw_split_phase1<R, true>(Ui, a.U, a.g, site0, sm);
         __syncthreads();
         Cx<R> o[3];
         int s, k0;
-        double dot = 0.0;
+        typename Acc<R>::T dot = Acc<R>::zero();
         if (hw_split_phase2<R, true>(Ui, a.g, site0, a.diag, sm, o, &s, &k0)) {
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
             const size_t e = (k0 + q) * (size_t)V + s;
             const Cx<R> u = ld<R, true>(Ui + e);
             const Cx<R> um = (i > 1) ? ld<R, true>(Um + e) : Cx<R>{R(0), R(0)};
-            const Cx<R> w = lz_w<R>(o[q], um, (R)inv_n, (R)cm, i == 1);
+            const Cx<R> w = lz_w<R>(o[q], um, inv_nR, cmR, i == 1);
             st<R>(W + e, w);
-            dot += (double)u.re * (double)w.re + (double)u.im * (double)w.im;
+            dot = Acc<R>::dot(dot, u, w);
           }
         }
-        const double bs = block_sum<NT1>(dot, sh);
+        const double bs = block_sum<NT1>(Acc<R>::get(dot), sh);
         if (tid == 0) s_part[r] += bs;
         __syncthreads();
       }
@@ -569,6 +670,7 @@ __global__ void __launch_bounds__(NT1, 4) lanczos_coop_kernel(SolveArgs<R> a, in
               S->iter = i;
               S->n_cur = s_ncur[r];
               S->n_prev = s_nprev[r];
+              set_norm_scalars(S);
               S->status = (act > 0 && !beta0) ? OV_ERR_NOT_CONVERGED : OV_OK;
               S->done = 1;
             }
@@ -601,18 +703,19 @@ __global__ void __launch_bounds__(NT1, 4) lanczos_coop_kernel(SolveArgs<R> a, in
       T* W = (T*)base + lz_slot(a.prm, i + 1) * n12;
       const double inv_n = 1.0 / s_ncur[r];
       const int s = site0 + lane;
-      double nrm = 0.0;
+      typename Acc<R>::T nrm = Acc<R>::zero();
+      const R inv_nR = (R)inv_n, alphaR = (R)s_alpha[r];
       if (s < V) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const size_t e = (3 * grp + q) * (size_t)V + s;
-          const Cx<R> v = lz_v<R>(ld<R, true>(Ui + e), (R)inv_n);
-          const Cx<R> u = lz_next<R>(ld<R, true>(W + e), v, (R)s_alpha[r]);
+          const Cx<R> v = lz_v<R>(ld<R, true>(Ui + e), inv_nR);
+          const Cx<R> u = lz_next<R>(ld<R, true>(W + e), v, alphaR);
           st<R>(W + e, u);
-          nrm += (double)u.re * (double)u.re + (double)u.im * (double)u.im;
+          nrm = Acc<R>::dot(nrm, u, u);
         }
       }
-      const double bs = block_sum<NT1>(nrm, sh);
+      const double bs = block_sum<NT1>(Acc<R>::get(nrm), sh);
       if (tid == 0) s_part[r] += bs;
       __syncthreads();
     }
@@ -675,27 +778,65 @@ __global__ void __launch_bounds__(NT1, 4) lanczos_coop_kernel(SolveArgs<R> a, in
   }
 }
 
+// Per-iteration scalars of the regeneration pass from the recorded alpha_i, beta_i and
+// the coefficients g_i, in the vector type -- with the same FP64 expressions (and
+// double-float splits) as the first pass, so the regenerated basis is bit-identical.
+template <typename R>
+__global__ void regen_scalars_kernel(SolveArgs<R> a, RegenRec<R>* rec, int nsrc) {
+  const int mi = a.prm->max_iter;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nsrc * mi; t += gridDim.x * blockDim.x) {
+    const int r = t / mi, i = t % mi + 1;
+    const SrcState* S = a.src + r;
+    if (i > S->k_final) continue;
+    const double n_i = (i == 1) ? S->bnorm : a.hist_b[(size_t)r * mi + i - 2];
+    const double n_m = (i <= 2) ? S->bnorm : a.hist_b[(size_t)r * mi + i - 3];
+    float d[6];
+    const double inv_n = 1.0 / n_i, cm = (i > 1) ? n_i / n_m : 0.0, alpha = a.hist_a[(size_t)r * mi + i - 1];
+    df_split(inv_n, d + 0);
+    df_split(cm, d + 2);
+    df_split(alpha, d + 4);
+    const double2 g = a.gco[(size_t)r * mi + i - 1];
+    RegenRec<R> o;
+    o.inv_n = scal<R>(inv_n, d + 0);
+    o.cm = scal<R>(cm, d + 2);
+    o.alpha = scal<R>(alpha, d + 4);
+    o.pad = o.alpha;
+    o.g = cx_from<R>(g.x, g.y);
+    rec[t] = o;
+  }
+}
+
 // Stored-basis variant of the second pass: sum[r][e] += sum_{i=1..k_r} gw[r][i-1] U_i[e],
-// gw = g_i / ||U_i|| (the basis is stored unnormalised).  Reads the basis once.
-__global__ void basis_sum_kernel(const double2* __restrict__ basis, int nslots, const double2* __restrict__ gw,
-                                 int ldg, const int* __restrict__ kr, double2* __restrict__ sum, size_t n12) {
+// gw = g_i / ||U_i|| (the basis is stored unnormalised), in the arithmetic of the basis
+// (FP64, or double-float with gw split into double-float pairs on the host); one read
+// of the basis and one FP64 update of the sum per element.
+template <typename R>
+__global__ void basis_sum_kernel(const typename Store<R>::T* __restrict__ basis, int nslots,
+                                 const typename Store<R>::T* __restrict__ gw, int ldg, const int* __restrict__ kr,
+                                 double2* __restrict__ sum, size_t n12) {
   const int r = blockIdx.y;
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n12) return;
-  const double2* B = basis + (size_t)r * nslots * n12 + e;
-  const double2* w = gw + (size_t)r * ldg;
-  double re = 0.0, im = 0.0;
+  const typename Store<R>::T* B = basis + (size_t)r * nslots * n12 + e;
+  const typename Store<R>::T* w = gw + (size_t)r * ldg;
+  Cx<R> acc = {R(0), R(0)};
   const int k = kr[r];
-  for (int i = 1; i <= k; ++i) {
-    const double2 u = __ldg(B + (size_t)i * n12);
-    const double2 c = __ldg(w + i - 1);
-    re = fma(c.x, u.x, fma(-c.y, u.y, re));
-    im = fma(c.x, u.y, fma(c.y, u.x, im));
-  }
+  for (int i = 1; i <= k; ++i) acc = cfma(ld<R>(w + i - 1), ld<R>(B + (size_t)i * n12), acc);
   double2 sv = sum[(size_t)r * n12 + e];
-  sv.x += re;
-  sv.y += im;
+  sv.x += (double)acc.re;
+  sv.y += (double)acc.im;
   sum[(size_t)r * n12 + e] = sv;
+}
+
+// sum += (double) ssum: the double-float regeneration-pass sum into the FP64 sum
+__global__ void fold_df_sum_kernel(const float4* __restrict__ ssum, double2* __restrict__ sum, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const float4 v = ssum[t];
+    double2 sv = sum[t];
+    sv.x += (double)v.x + (double)v.y;
+    sv.y += (double)v.z + (double)v.w;
+    sum[t] = sv;
+  }
 }
 
 // Init: U_1 = b (ring slot 1), ||b|| per source, s = c0 b, node states reset.
@@ -712,10 +853,7 @@ __global__ void __launch_bounds__(NT2) lanczos_init_kernel(SolveArgs<R> a, const
   double nrm = 0.0;
   if (e < n12) {
     const double2 bv = b[(size_t)r * n12 + e];
-    T t;
-    t.x = bv.x;
-    t.y = bv.y;
-    U1[e] = t;
+    st<R>(U1 + e, cx_from<R>(bv.x, bv.y));
     nrm = bv.x * bv.x + bv.y * bv.y;
     if (a.sacc) a.sacc[(size_t)r * n12 + e] = make_double2(c0.x * bv.x - c0.y * bv.y, c0.x * bv.y + c0.y * bv.x);
   }
@@ -738,6 +876,7 @@ __global__ void __launch_bounds__(NT2) lanczos_init_kernel(SolveArgs<R> a, const
   S->n_prev = 1.0;
   S->alpha = 0.0;
   S->iter = 1;
+  set_norm_scalars(S);
   S->status = OV_OK;
   S->n_act = 0;
   S->node_updates = 0.0;
@@ -772,23 +911,16 @@ __global__ void ring_reset_kernel(SolveArgs<R> a, const double2* __restrict__ b,
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
     const size_t r = t / n12, e = t % n12;
     const double2 bv = b[t];
-    T v;
-    v.x = bv.x;
-    v.y = bv.y;
-    a.ring[r * nslots * n12 + n12 + e] = v;
+    st<R>(a.ring + r * nslots * n12 + n12 + e, cx_from<R>(bv.x, bv.y));
   }
 }
 
 // zero the per-node solution buffers (first update writes them, but a node that is
 // converged at init must still read as zero)
-template <typename T>
-__global__ void zero_kernel(T* p, size_t n) {
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    T z;
-    z.x = 0;
-    z.y = 0;
-    p[t] = z;
-  }
+template <typename R>
+__global__ void zero_kernel(typename Store<R>::T* p, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    st<R>(p + t, Cx<R>{R(0), R(0)});
 }
 
 }  // namespace
@@ -796,6 +928,29 @@ __global__ void zero_kernel(T* p, size_t n) {
 // ------------------------------------------------------------------ host side
 
 namespace {
+
+// workspace name prefix per arithmetic type of the coefficient-space forms
+template <typename R> const char* coef_tag();
+template <> const char* coef_tag<double>() { return "fp64"; }
+template <> const char* coef_tag<DF>() { return "df"; }
+
+// a complex coefficient in the storage type of the vectors (host side)
+inline double2 host_store(double2 v, double2*) { return v; }
+inline float4 host_store(double2 v, float4*) {
+  const float rh = (float)v.x, ih = (float)v.y;
+  return make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+}
+
+// link planes and host-side scalar conversion per arithmetic type
+template <typename R> const typename Store<R>::T* solver_links(ov_ctx* ctx);
+template <> const double2* solver_links<double>(ov_ctx* ctx) { return ctx->U64; }
+template <> const float2* solver_links<float>(ov_ctx* ctx) { return ctx->U32; }
+template <> const float4* solver_links<DF>(ov_ctx* ctx) { return ctx->Udf; }
+template <typename R> R solver_real(double x) { return (R)x; }
+template <> DF solver_real<DF>(double x) {
+  const float h = (float)x;
+  return DF(h, (float)(x - (double)h));
+}
 
 template <typename R>
 struct SolveWs {
@@ -814,10 +969,13 @@ int setup_ws(ov_ctx* ctx, int nsrc, int ns, bool want_x, bool want_sacc, bool wa
   int st = OV_OK;
   std::string t(tag);
   w->nblk1 = (V + kSplitSites - 1) / kSplitSites;
-  // K2 runs grid-stride with about two blocks per SM in total (at least 8 per source);
-  // the init kernel uses the same partial buffer with up to ceil(12V / NT2) blocks
+  // the init kernel uses the K2 partial buffer with up to ceil(12V / NT2) blocks
   w->nblk2 = (int)((n12 + NT2 - 1) / NT2);
-  w->nblk2u = (int)std::min<size_t>(w->nblk2, std::max<size_t>(8, (size_t)(2 * 152) / (size_t)nsrc));
+  // K2 is a grid-stride loop: about two blocks per SM in total when the vectors are small
+  // (fewer partials, short tail), up to eight (full occupancy, enough loads in flight for
+  // HBM) when every thread would otherwise stride over more than 8 elements
+  const size_t want = std::min<size_t>(8 * 152, std::max<size_t>(2 * 152, (size_t)nsrc * n12 / (NT2 * 8)));
+  w->nblk2u = (int)std::min<size_t>(w->nblk2, std::max<size_t>(8, want / (size_t)nsrc));
   auto& a = w->a;
   w->nslots = nslots;
   a.ring = (T*)ws_get(ctx, (t + ".ring").c_str(), sizeof(T) * (size_t)nslots * n12 * nsrc, &st);
@@ -849,11 +1007,8 @@ int setup_ws(ov_ctx* ctx, int nsrc, int ns, bool want_x, bool want_sacc, bool wa
   a.prm = w->prm_dev;
   a.stencil = nullptr;
   a.g = ctx->g;
-  a.diag = (R)(4.0 - ctx->m0);
-  if (sizeof(R) == 8)
-    a.U = (const T*)ctx->U64;
-  else
-    a.U = (const T*)ctx->U32;
+  a.diag = solver_real<R>(4.0 - ctx->m0);
+  a.U = solver_links<R>(ctx);
   return st;
 }
 
@@ -974,7 +1129,7 @@ int init_solve(ov_ctx* ctx, SolveWs<R>& w, const double2* b_soa, int nsrc, int n
   cudaMemsetAsync(w.a.done_count, 0, sizeof(int), s);
   if (w.a.x) {
     const size_t n = (size_t)12 * ctx->g.V * nsrc * ns;
-    zero_kernel<typename Store<R>::T><<<1024, 256, 0, s>>>(w.a.x, n);
+    zero_kernel<R><<<1024, 256, 0, s>>>(w.a.x, n);
   }
   cudaEvent_t ev;
   kt_begin(ctx, KC_MISC, s, &ev);
@@ -1107,12 +1262,14 @@ static void lanczos_sum_coefficients(const ov_ctx* ctx, int nsrc, const std::vec
 
 // Stored-basis form of OV_MODE_FP64_2PASS: pass 1 keeps U_1 .. U_k (slot i), then
 // s = c0 b + sum_i (g_i / ||U_i||) U_i in one read of the basis.
+template <typename R>
 static int solve_sign_stored(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc,
                              const ov_solve_opts& o, SolveOut* so, cudaStream_t s, int cap) {
   const int ns = (int)ctx->z.size();
   const size_t n12 = (size_t)12 * ctx->g.V;
-  SolveWs<double> w;
-  int st = setup_ws<double>(ctx, nsrc, ns, false, true, true, cap, &w, "fp64s", cap + 3);
+  SolveWs<R> w;
+  const std::string tag = std::string(coef_tag<R>()) + "s";
+  int st = setup_ws<R>(ctx, nsrc, ns, false, true, true, cap, &w, tag.c_str(), cap + 3);
   if (st != OV_OK) return st;
   std::vector<double2> zh((size_t)nsrc * ns), ch((size_t)nsrc * ns);
   for (int r = 0; r < nsrc; ++r)
@@ -1120,13 +1277,13 @@ static int solve_sign_stored(ov_ctx* ctx, const double2* b_soa, double2* out_soa
       zh[(size_t)r * ns + j] = ctx->z[j];
       ch[(size_t)r * ns + j] = ctx->c[j];
     }
-  st = init_solve<double>(ctx, w, b_soa, nsrc, ns, zh, ch, ctx->c0, o.tol, cap, s, 0);
+  st = init_solve<R>(ctx, w, b_soa, nsrc, ns, zh, ch, ctx->c0, o.tol, cap, s, 0);
   if (st != OV_OK) return st;
   double launches = 1.0;
-  st = run_coop<double>(ctx, w, nsrc, s, &launches);
-  if (st == OV_ERR_INVALID_ARG) st = run_iterations<double>(ctx, w, nsrc, ns, 6, cap, o, s, &launches);
+  st = run_coop<R>(ctx, w, nsrc, s, &launches);
+  if (st == OV_ERR_INVALID_ARG) st = run_iterations<R>(ctx, w, nsrc, ns, 6, cap, o, s, &launches);
   if (st != OV_OK) return st;
-  const int fst = finish_solve<double>(ctx, w, nsrc, ns, zh, ch, so, s);
+  const int fst = finish_solve<R>(ctx, w, nsrc, ns, zh, ch, so, s);
   // not converged within the store: the caller regenerates, unless the store already
   // spans max_iter (then the best iterate is returned with OV_ERR_NOT_CONVERGED)
   if (fst != OV_OK && !(fst == OV_ERR_NOT_CONVERGED && cap >= o.max_iter)) return fst;
@@ -1151,15 +1308,18 @@ static int solve_sign_stored(ov_ctx* ctx, const double2* b_soa, double2* out_soa
       g[(size_t)r * cap + i].x /= ni;
       g[(size_t)r * cap + i].y /= ni;
     }
-  double2* gd = (double2*)ws_get(ctx, "fp64s.g", sizeof(double2) * g.size(), &st);
-  int* krd = (int*)ws_get(ctx, "fp64s.kr", sizeof(int) * nsrc, &st);
+  using T = typename Store<R>::T;
+  std::vector<T> gs(g.size());
+  for (size_t t = 0; t < g.size(); ++t) gs[t] = host_store(g[t], (T*)nullptr);
+  T* gd = (T*)ws_get(ctx, (tag + ".g").c_str(), sizeof(T) * gs.size(), &st);
+  int* krd = (int*)ws_get(ctx, (tag + ".kr").c_str(), sizeof(int) * nsrc, &st);
   if (st != OV_OK) return st;
-  e = cudaMemcpyAsync(gd, g.data(), sizeof(double2) * g.size(), cudaMemcpyHostToDevice, s);
+  e = cudaMemcpyAsync(gd, gs.data(), sizeof(T) * gs.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(krd, kr.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy coefficients");
   cudaEvent_t ev;
   kt_begin(ctx, KC_REGEN, s, &ev);
-  basis_sum_kernel<<<dim3((unsigned)((n12 + 255) / 256), nsrc), 256, 0, s>>>(w.a.ring, cap + 3, gd, cap, krd,
+  basis_sum_kernel<R><<<dim3((unsigned)((n12 + 255) / 256), nsrc), 256, 0, s>>>(w.a.ring, cap + 3, gd, cap, krd,
                                                                              w.a.sacc, n12);
   kt_end(ctx, KC_REGEN, s, ev);
   OV_CHECK_LAUNCH(ctx, "basis_sum_kernel");
@@ -1176,8 +1336,9 @@ static int solve_sign_stored(ov_ctx* ctx, const double2* b_soa, double2* out_soa
 // regenerate v_1 .. v_k with bit-identical arithmetic and accumulate
 // s = c0 b + sum_i g_i v_i.  Same result as OV_MODE_FP64 up to rounding; the vector
 // work no longer grows with the number of nodes.
-int solve_sign_2pass(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc, const ov_solve_opts& o,
-                     SolveOut* so, cudaStream_t s) {
+template <typename R>
+static int solve_sign_coef(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc, const ov_solve_opts& o,
+                           SolveOut* so, cudaStream_t s) {
   const int ns = (int)ctx->z.size();
   // Keep the whole basis in HBM when up to min(max_iter, 1024) vectors per source fit a
   // quarter of the device: then pass 2 is one read of the basis instead of a second
@@ -1186,15 +1347,22 @@ int solve_sign_2pass(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int ns
   cudaMemGetInfo(&freeb, &totalb);
   const int cap = std::min(o.max_iter, 1024);
   const double store_bytes = (double)(cap + 2) * nsrc * 12.0 * ctx->g.V * sizeof(double2);
-  if (o.mode == OV_MODE_FP64_2PASS && store_bytes <= 0.25 * (double)totalb) {
-    const int st = solve_sign_stored(ctx, b_soa, out_soa, nsrc, o, so, s, cap);
+  if (o.mode != OV_MODE_FP64_REGEN && store_bytes <= 0.25 * (double)totalb) {
+    const int st = solve_sign_stored<R>(ctx, b_soa, out_soa, nsrc, o, so, s, cap);
     if (st != OV_ERR_NOT_CONVERGED || cap >= o.max_iter) return st;
   }
-  SolveWs<double> w;
-  int st = setup_ws<double>(ctx, nsrc, ns, false, true, true, o.max_iter, &w, "fp64");
+  SolveWs<R> w;
+  const std::string tag = coef_tag<R>();
+  int st = setup_ws<R>(ctx, nsrc, ns, false, true, true, o.max_iter, &w, tag.c_str());
   if (st != OV_OK) return st;
-  double2* gco = (double2*)ws_get(ctx, "fp64.gco", sizeof(double2) * (size_t)nsrc * o.max_iter, &st);
+  double2* gco = (double2*)ws_get(ctx, (tag + ".gco").c_str(), sizeof(double2) * (size_t)nsrc * o.max_iter, &st);
   if (st != OV_OK) return st;
+  const size_t n12 = (size_t)12 * ctx->g.V;
+  float4* ssum = nullptr;
+  if (std::is_same<R, DF>::value) {
+    ssum = (float4*)ws_get(ctx, "df.ssum", sizeof(float4) * n12 * nsrc, &st);
+    if (st != OV_OK) return st;
+  }
   w.a.p = nullptr;
   std::vector<double2> zh((size_t)nsrc * ns), ch((size_t)nsrc * ns);
   for (int r = 0; r < nsrc; ++r)
@@ -1202,12 +1370,12 @@ int solve_sign_2pass(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int ns
       zh[(size_t)r * ns + j] = ctx->z[j];
       ch[(size_t)r * ns + j] = ctx->c[j];
     }
-  st = init_solve<double>(ctx, w, b_soa, nsrc, ns, zh, ch, ctx->c0, o.tol, o.max_iter, s, 0);
+  st = init_solve<R>(ctx, w, b_soa, nsrc, ns, zh, ch, ctx->c0, o.tol, o.max_iter, s, 0);
   if (st != OV_OK) return st;
   double launches = 1.0;
-  st = run_iterations<double>(ctx, w, nsrc, ns, 2, o.max_iter, o, s, &launches);
+  st = run_iterations<R>(ctx, w, nsrc, ns, 2, o.max_iter, o, s, &launches);
   if (st != OV_OK) return st;
-  const int fst = finish_solve<double>(ctx, w, nsrc, ns, zh, ch, so, s);
+  const int fst = finish_solve<R>(ctx, w, nsrc, ns, zh, ch, so, s);
   if (fst != OV_OK && fst != OV_ERR_NOT_CONVERGED) return fst;
   // coefficients of the sum in the Lanczos basis
   std::vector<SrcState> S(nsrc);
@@ -1239,8 +1407,19 @@ int solve_sign_2pass(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int ns
   if (e == cudaSuccess) e = cudaMemsetAsync(w.a.cnt, 0, sizeof(unsigned) * 2 * nsrc, s);
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "second-pass setup");
   w.a.gco = gco;
-  ring_reset_kernel<double><<<256, 256, 0, s>>>(w.a, b_soa, nsrc, 3);
-  launches += 1.0;
+  w.a.ssum = (typename Store<R>::T*)ssum;
+  RegenRec<R>* rrec =
+      (RegenRec<R>*)ws_get(ctx, (tag + ".rrec").c_str(), sizeof(RegenRec<R>) * (size_t)nsrc * o.max_iter, &st);
+  if (st != OV_OK) return st;
+  w.a.rrec = rrec;
+  regen_scalars_kernel<R><<<64, 256, 0, s>>>(w.a, rrec, nsrc);
+  OV_CHECK_LAUNCH(ctx, "regen_scalars_kernel");
+  ring_reset_kernel<R><<<256, 256, 0, s>>>(w.a, b_soa, nsrc, 3);
+  launches += 2.0;
+  if (ssum) {
+    e = cudaMemsetAsync(ssum, 0, sizeof(float4) * n12 * nsrc, s);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "clear double-float sum");
+  }
   // pass 2: kmax regeneration launches (no host reads), replayed from a graph
   const int chunk = o.check_every > 0 ? o.check_every : 32;
   const bool graph = o.use_graph && !ctx->timing;
@@ -1255,7 +1434,7 @@ int solve_sign_2pass(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int ns
       cudaError_t ce = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
       if (ce != cudaSuccess) return ctx_cuda(ctx, ce, "cudaStreamBeginCapture");
       for (int k = 0; k < chunk; ++k)
-        lanczos_regen_kernel<double><<<dim3(w.nblk1, nsrc), NT1, 0, ctx->cap_stream>>>(w.a);
+        lanczos_regen_kernel<R><<<dim3(w.nblk1, nsrc), NT1, 0, ctx->cap_stream>>>(w.a);
       cudaGraph_t gph = nullptr;
       ce = cudaStreamEndCapture(ctx->cap_stream, &gph);
       if (ce != cudaSuccess) return ctx_cuda(ctx, ce, "cudaStreamEndCapture");
@@ -1275,7 +1454,7 @@ int solve_sign_2pass(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int ns
       for (int k = 0; k < n; ++k) {
         cudaEvent_t ev;
         kt_begin(ctx, KC_REGEN, s, &ev);
-        lanczos_regen_kernel<double><<<dim3(w.nblk1, nsrc), NT1, 0, s>>>(w.a);
+        lanczos_regen_kernel<R><<<dim3(w.nblk1, nsrc), NT1, 0, s>>>(w.a);
         kt_end(ctx, KC_REGEN, s, ev);
       }
       OV_CHECK_LAUNCH(ctx, "lanczos_regen_kernel");
@@ -1283,11 +1462,25 @@ int solve_sign_2pass(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int ns
     done += n;
     launches += n;
   }
+  if (ssum) {
+    fold_df_sum_kernel<<<152 * 8, 256, 0, s>>>(ssum, w.a.sacc, n12 * nsrc);
+    OV_CHECK_LAUNCH(ctx, "fold_df_sum_kernel");
+    launches += 1.0;
+  }
   so->launches = launches + 2.0;
-  e = cudaMemcpyAsync(out_soa, w.a.sacc, sizeof(double2) * 12 * (size_t)ctx->g.V * nsrc,
-                      cudaMemcpyDeviceToDevice, s);
+  e = cudaMemcpyAsync(out_soa, w.a.sacc, sizeof(double2) * n12 * nsrc, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy sum");
   return fst;
+}
+
+int solve_sign_2pass(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc, const ov_solve_opts& o,
+                     SolveOut* so, cudaStream_t s) {
+  if (o.mode == OV_MODE_F32X2) {
+    const int st = ensure_links_df(ctx, s);
+    if (st != OV_OK) return st;
+    return solve_sign_coef<DF>(ctx, b_soa, out_soa, nsrc, o, so, s);
+  }
+  return solve_sign_coef<double>(ctx, b_soa, out_soa, nsrc, o, so, s);
 }
 
 // OV_MODE_MIXED.

@@ -25,11 +25,11 @@ OV_ERR_NO_CONTOUR = 7
 OV_ERR_SCRATCH_TOO_SMALL = 8
 
 OV_FP64, OV_FP32 = 0, 1
-OV_MODE_FP64, OV_MODE_MIXED, OV_MODE_FP64_2PASS, OV_MODE_FP64_REGEN = 0, 1, 2, 3
+OV_MODE_FP64, OV_MODE_MIXED, OV_MODE_FP64_2PASS, OV_MODE_FP64_REGEN, OV_MODE_F32X2 = 0, 1, 2, 3, 4
 OV_CONTOUR_SINGLE, OV_CONTOUR_PAIR = 0, 1
 
 MODES = {"fp64": OV_MODE_FP64, "mixed": OV_MODE_MIXED, "fp64_2pass": OV_MODE_FP64_2PASS,
-         "fp64_regen": OV_MODE_FP64_REGEN}
+         "fp64_regen": OV_MODE_FP64_REGEN, "f32x2": OV_MODE_F32X2}
 
 # every symbol include/ov.h declares
 EXPORTS = (

@@ -23,7 +23,7 @@ def _oracle(U, b, ctx, tol=1e-13):
     return out
 
 
-@pytest.mark.parametrize("mode", ["fp64", "fp64_2pass", "fp64_regen"])
+@pytest.mark.parametrize("mode", ["fp64", "fp64_2pass", "fp64_regen", "f32x2"])
 def test_config1_4x4_dense(gpu_lib, mode):
     """4^4, eps = 0.3, N_q = 32 from Lanczos placement: parity with the per-node oracle,
     accuracy vs dense zheevd sgn, GW relation and sgn^2 = 1 within the predicted error."""
@@ -71,7 +71,7 @@ def config2(gpu_lib):
     return ctx, U, b, spec, want0
 
 
-@pytest.mark.parametrize("mode", ["fp64", "fp64_2pass", "fp64_regen"])
+@pytest.mark.parametrize("mode", ["fp64", "fp64_2pass", "fp64_regen", "f32x2"])
 def test_config2_8x4_parity(gpu_lib, config2, mode):
     """tol 1e-12, 4 sources in one call; source 0 against the per-node CGNR oracle at 1e-10,
     all four: sgn^2 b = b within the predicted method error."""
@@ -88,7 +88,7 @@ def test_config2_8x4_parity(gpu_lib, config2, mode):
         assert rel(s2[k], b[k]) < max(10 * spec["predicted_error"], 1e-9)
 
 
-@pytest.mark.parametrize("mode", ["fp64_2pass", "fp64_regen"])
+@pytest.mark.parametrize("mode", ["fp64_2pass", "fp64_regen", "f32x2"])
 def test_two_pass_equals_shifted(gpu_lib, config2, mode):
     """The coefficient-space forms (stored basis, regenerated basis) and the vector-space
     shifted form compute the same Galerkin iterates: agreement to rounding, per source."""
@@ -104,7 +104,7 @@ def test_two_pass_equals_shifted(gpu_lib, config2, mode):
     assert sc["node_updates"] == 0 and sa["node_updates"] > 0
 
 
-@pytest.mark.parametrize("mode", ["fp64", "fp64_2pass", "fp64_regen"])
+@pytest.mark.parametrize("mode", ["fp64", "fp64_2pass", "fp64_regen", "f32x2"])
 def test_ragged_lattice_parity(gpu_lib, mode):
     """Lattice whose volume is not a multiple of any block size; 3 sources."""
     dims = (3, 5, 4, 6)
@@ -175,7 +175,7 @@ def test_graph_and_direct_launch_agree_bitwise(gpu_lib):
     assert np.array_equal(a1, a2)
 
 
-@pytest.mark.parametrize("mode", ["fp64", "fp64_2pass", "fp64_regen"])
+@pytest.mark.parametrize("mode", ["fp64", "fp64_2pass", "fp64_regen", "f32x2"])
 def test_edge_cases(gpu_lib, mode):
     import torch
 
