@@ -55,16 +55,34 @@ def _twist(x, bc_t, sign):
     return x * ph.reshape((lt, 1, 1, 1, 1, 1))
 
 
-def apply_function(x, f, m0, r=1.0, bc_t=-1.0):
-    """f(H_W[U=1]) x for a canonical spinor array x (..., Lt, Lz, Ly, Lx, 4, 3)."""
-    x = np.asarray(x, dtype=np.complex128)
-    shp = x.shape[-6:-2]
-    H, E = hamiltonian_p(shp, m0, r, bc_t)
+def _function_p(shape_tzyx, f, m0, r, bc_t):
+    """f(H(p)) as an array (Lt, Lz, Ly, Lx, 4, 4)."""
+    H, E = hamiltonian_p(shape_tzyx, m0, r, bc_t)
     fp, fm = f(E), f(-E)
-    F = 0.5 * (fp + fm)[..., None, None] * np.eye(4) + (0.5 * (fp - fm) / E)[..., None, None] * H
+    return 0.5 * (fp + fm)[..., None, None] * np.eye(4) + (0.5 * (fp - fm) / E)[..., None, None] * H
+
+
+def _apply_p(x, F, bc_t):
+    """Apply a spin matrix per momentum, F (Lt, Lz, Ly, Lx, 4, 4), to a canonical spinor array."""
     B = np.fft.fftn(_twist(x, bc_t, -1), axes=_SITE_AXES)
     B = np.einsum("...st,...tc->...sc", F, B)
     return _twist(np.fft.ifftn(B, axes=_SITE_AXES), bc_t, +1)
+
+
+def apply_function(x, f, m0, r=1.0, bc_t=-1.0):
+    """f(H_W[U=1]) x for a canonical spinor array x (..., Lt, Lz, Ly, Lx, 4, 3)."""
+    x = np.asarray(x, dtype=np.complex128)
+    return _apply_p(x, _function_p(x.shape[-6:-2], f, m0, r, bc_t), bc_t)
+
+
+def overlap_inverse(x, f, m_q, m0, r=1.0, bc_t=-1.0):
+    """D_ov(m_q)^-1 x at U = 1, with the sign function replaced by f (the exact sign, or the
+    rational function r_N of a quadrature): per momentum D(p) = (1 + m_q)/2 + (1 - m_q)/2
+    gamma5 f(H(p)) (Eq. 1) is a 4 x 4 spin matrix, inverted directly."""
+    x = np.asarray(x, dtype=np.complex128)
+    S = _function_p(x.shape[-6:-2], f, m0, r, bc_t)
+    D = 0.5 * (1.0 + m_q) * np.eye(4) + 0.5 * (1.0 - m_q) * np.einsum("su,...ut->...st", gamma5(), S)
+    return _apply_p(x, np.linalg.inv(D), bc_t)
 
 
 def apply_H(x, m0, r=1.0, bc_t=-1.0):

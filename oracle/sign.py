@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import contour
 from .gamma import gamma5
 from .wilson import apply_HW
 
@@ -108,6 +109,24 @@ def sigma(y, s):
     """Quality of the sign function: |s^dag s - y^dag y| / y^dag y with s = sgn(H) y."""
     yy = np.vdot(y, y).real
     return abs(np.vdot(s, s).real - yy) / yy
+
+
+def overlap_dense(H, z, c, c0, m_q):
+    """Dense D_ov(m_q) = (1 + m_q)/2 + (1 - m_q)/2 gamma5 S_N (Eq. 1), with the quadrature
+    operator S_N = V r_N(Lambda) V^dag, r_N(lambda) = c0 + sum_j c_j / (z_j - lambda)
+    (Eqs. 5, 7 on the eigenbasis of H).  Tiny lattices only."""
+    lam, V = np.linalg.eigh(H)
+    rN = contour.rational(lam, z, c, c0)
+    S = (V * rN[None, :]) @ V.conj().T
+    n = H.shape[0]
+    g = np.tile(np.repeat([1.0, 1.0, -1.0, -1.0], 3), n // 12)
+    return 0.5 * (1.0 + m_q) * np.eye(n) + 0.5 * (1.0 - m_q) * g[:, None] * S
+
+
+def overlap_solve_dense(H, b, z, c, c0, m_q):
+    """x = D_ov(m_q)^-1 b by LU on the dense operator: the solve the overlap propagator
+    needs (each of its matrix-vector products is one D_ov apply, Eq. 1)."""
+    return np.linalg.solve(overlap_dense(H, z, c, c0, m_q), np.asarray(b, dtype=np.complex128).reshape(-1))
 
 
 def gw_residual(apply_D0, x):
