@@ -201,6 +201,22 @@ int ov_sgn_vjp(ov_ctx* ctx, const void* eta, const void* b, void* grad_b, double
 int ov_overlap_vjp(ov_ctx* ctx, double m_q, const void* eta, const void* b, void* grad_b,
                    double* grad_links, const ov_solve_opts* opts, ov_stats* stats, void* stream);
 
+/* Overlap solve: x = D_ov(m_q)^-1 b (Eq. 1 with the quadrature sign S_N of Eqs. 5-7), for
+ * nrhs sources at once, by conjugate gradients on the normal equations
+ * D^dag D x = D^dag b with D^dag = gamma5 D gamma5 (exact for the hermitian S_N).  Every
+ * CG iteration applies D twice (each a full shifted solve with the options in `inner`;
+ * NULL = defaults).  b, x: canonical complex128 spinors [nrhs][t][z][y][x][4][3], device
+ * pointers (host pointers when inner->host_io), b != x; the caller owns both.  Stops a
+ * source when ||D^dag (b - D x)|| <= tol ||D^dag b||; tol in (0, 1); at most max_iter
+ * iterations.  stats: iterations = CG iterations, refine_rounds = D applies,
+ * inner_iterations = Krylov iterations of all applies, max_residual = max over sources
+ * of the true ||b - D x|| / ||b|| (one extra apply), error_bound = max normal-equation
+ * residual.  Errors: OV_ERR_INVALID_ARG, OV_ERR_NO_GAUGE, OV_ERR_NO_CONTOUR,
+ * OV_ERR_NOT_CONVERGED (x holds the last iterate; also when an inner solve misses its
+ * tolerance), OV_ERR_BREAKDOWN, OV_ERR_OUT_OF_MEMORY, OV_ERR_CUDA.  A zero source gives x = 0. */
+int ov_overlap_solve(ov_ctx* ctx, double m_q, const void* b, void* x, int nrhs, const ov_solve_opts* inner,
+                     double tol, int max_iter, ov_stats* stats, void* stream);
+
 /* FP32 stencil selection for ov_apply_HW(OV_FP32) and the FP32 phases of the mixed
  * solve.  Variants differ in right-hand sides per thread (link loads reused across
  * them), 12-real link compression (row 2 rebuilt as conj(row0 x row1)) and block
@@ -209,7 +225,9 @@ int ov_overlap_vjp(ov_ctx* ctx, double m_q, const void* eta, const void* b, void
  * of variants and, for 0 <= k < count, describes variant k.  compressed: 0 plain
  * links, 1 12-real links (structure-of-arrays float2 layout); 2 right-hand-side-paired
  * layout with paired FP32 instructions and broadcast links; 3 and 4 spin-paired float4
- * layout (one 16-byte load per spin pair) with plain (padded) or 12-real links. */
+ * layout (one 16-byte load per spin pair) with plain (padded) or 12-real links.
+ * rhs_tile 0: four threads per site (one per direction), partial sums combined in
+ * shared memory. */
 int ov_set_hw32_variant(ov_ctx* ctx, int k);
 int ov_hw32_variants(int k, int* rhs_tile, int* compressed, int* threads);
 

@@ -100,19 +100,7 @@ void kt_collect(ov_ctx* ctx) {
   ctx->pending.clear();
 }
 
-namespace {
-
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
+// ------------------------------------------------ helpers of the entry points
 
 ov_solve_opts resolve_opts(const ov_solve_opts* o) {
   ov_solve_opts r;
@@ -187,8 +175,6 @@ void fill_stats(ov_stats* st, const SolveOut& so, double ms) {
   st->node_updates = so.node_updates;
   st->launches = so.launches;
 }
-
-}  // namespace
 
 // ------------------------------------------------------------------ ABI
 

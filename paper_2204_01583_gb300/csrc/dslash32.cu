@@ -146,6 +146,29 @@ __global__ void compress_links_kernel(const float2* __restrict__ u32, float2* __
   }
 }
 
+// Four threads per site (one per direction), the partial hop sums combined through
+// shared memory (hw_split_phase1/2): four times the threads of the tile kernel for the
+// same work, so more loads are in flight per SM.  Uncompressed links.
+__global__ void __launch_bounds__(kSplitNT) hw32_split_kernel(const float2* __restrict__ in, float2* __restrict__ out,
+                                                             const float2* __restrict__ U, Geom g, float diag) {
+  __shared__ Cx<float> sm[4 * 12 * kSplitSites];
+  const size_t off = (size_t)blockIdx.y * 12 * g.V;
+  const int site0 = blockIdx.x * kSplitSites;
+  hw_split_phase1<float>(in + off, U, g, site0, sm);
+  __syncthreads();
+  Cx<float> o[3];
+  int s, k0;
+  if (hw_split_phase2<float>(in + off, g, site0, diag, sm, o, &s, &k0)) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) st<float>(out + off + (k0 + q) * (size_t)g.V + s, o[q]);
+  }
+}
+
+void launch_split(const float2* in, float2* out, const float2* U, Geom g, float diag, int nrhs, cudaStream_t s) {
+  dim3 grid((g.V + kSplitSites - 1) / kSplitSites, nrhs);
+  hw32_split_kernel<<<grid, kSplitNT, 0, s>>>(in, out, U, g, diag);
+}
+
 template <int RT, bool COMP, int NT>
 void launch_variant(const float2* in, float2* out, const float2* U, Geom g, float diag, int nrhs, cudaStream_t s) {
   dim3 grid((g.V + NT - 1) / NT, (nrhs + RT - 1) / RT);
@@ -166,6 +189,7 @@ const Cand kCands[] = {
     {2, false, 128, launch_variant<2, false, 128>}, {2, true, 128, launch_variant<2, true, 128>},
     {4, true, 128, launch_variant<4, true, 128>},   {4, true, 64, launch_variant<4, true, 64>},
     {2, true, 256, launch_variant<2, true, 256>},   {1, true, 256, launch_variant<1, true, 256>},
+    {0, false, kSplitNT, launch_split},  // rhs tile 0: four threads per site
 };
 constexpr int kNCands = sizeof(kCands) / sizeof(kCands[0]);
 

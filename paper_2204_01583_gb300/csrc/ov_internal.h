@@ -171,6 +171,31 @@ struct SolveOut {
   double node_updates = 0.0;
   double launches = 0.0;
 };
+// Makes ctx's device current for the scope of an entry point.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Helpers of the entry points (api.cu): defaults for null options, option checks, a
+// host clock, staging of host input (host_io), the sign function of canonical device
+// sources into a structure-of-arrays workspace, and the stats copy.
+ov_solve_opts resolve_opts(const ov_solve_opts* o);
+int check_opts(ov_ctx* ctx, const ov_solve_opts& o);
+double now_ms();
+const double2* stage_in(ov_ctx* ctx, const void* p, size_t bytes, int host_io, const char* name, cudaStream_t s,
+                        int* st);
+int sign_core(ov_ctx* ctx, const double2* b_dev, int nrhs, const ov_solve_opts& o, SolveOut* so, cudaStream_t s,
+              double2** s_soa_out, double2* xs);
+void fill_stats(ov_stats* st, const SolveOut& so, double ms);
+
 int solve_sign_soa(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nrhs,
                    const ov_solve_opts& o, SolveOut* so, cudaStream_t s,
                    double2* xs_soa /* optional per-node solutions [src][node][12V] */);

@@ -1,0 +1,250 @@
+// Overlap solve: x = D_ov(m_q)^-1 b by conjugate gradients on the normal equations
+// D^dag D x = D^dag b, every matrix-vector product an overlap apply (Eq. 1 with the
+// quadrature sign of Eqs. 5-7).  D^dag = gamma5 D gamma5 holds exactly for the hermitian
+// quadrature operator S_N, so one CG iteration costs two applies: D p, then
+// gamma5 D gamma5 (D p).  All sources advance together (every apply batches them);
+// per-source scalars live on the host, the vectors stay on the device in the canonical
+// layout.  Inner products are block partial sums reduced on the host in a fixed order.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int kNT = 256;
+constexpr int kDotBlocks = 64;  // partial sums per source
+
+// part[r][blk] = sum over this block's elements of Re(conj(u) v), source r = blockIdx.y
+__global__ void __launch_bounds__(kNT) cg_dot_kernel(const double2* __restrict__ u, const double2* __restrict__ v,
+                                                     double* __restrict__ part, size_t n12) {
+  __shared__ double sh[kNT / 32];
+  const size_t base = (size_t)blockIdx.y * n12;
+  double acc = 0.0;
+  for (size_t e = (size_t)blockIdx.x * kNT + threadIdx.x; e < n12; e += (size_t)gridDim.x * kNT) {
+    const double2 a = u[base + e], b = v[base + e];
+    acc = fma(a.x, b.x, fma(a.y, b.y, acc));
+  }
+  const double t = block_sum<kNT>(acc, sh);
+  if (threadIdx.x == 0) part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+// x += alpha_r p, r -= alpha_r q, and partials of ||r||^2
+__global__ void __launch_bounds__(kNT) cg_xr_kernel(double2* __restrict__ x, double2* __restrict__ r,
+                                                    const double2* __restrict__ p, const double2* __restrict__ q,
+                                                    const double* __restrict__ alpha, double* __restrict__ part,
+                                                    size_t n12) {
+  __shared__ double sh[kNT / 32];
+  const size_t base = (size_t)blockIdx.y * n12;
+  const double a = alpha[blockIdx.y];
+  double acc = 0.0;
+  for (size_t e = (size_t)blockIdx.x * kNT + threadIdx.x; e < n12; e += (size_t)gridDim.x * kNT) {
+    const size_t k = base + e;
+    const double2 pv = p[k], qv = q[k];
+    double2 xv = x[k], rv = r[k];
+    xv.x = fma(a, pv.x, xv.x);
+    xv.y = fma(a, pv.y, xv.y);
+    rv.x = fma(-a, qv.x, rv.x);
+    rv.y = fma(-a, qv.y, rv.y);
+    x[k] = xv;
+    r[k] = rv;
+    acc = fma(rv.x, rv.x, fma(rv.y, rv.y, acc));
+  }
+  const double t = block_sum<kNT>(acc, sh);
+  if (threadIdx.x == 0) part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+// p = r + beta_r p
+__global__ void __launch_bounds__(kNT) cg_p_kernel(double2* __restrict__ p, const double2* __restrict__ r,
+                                                   const double* __restrict__ beta, size_t n12) {
+  const size_t base = (size_t)blockIdx.y * n12;
+  const double bt = beta[blockIdx.y];
+  for (size_t e = (size_t)blockIdx.x * kNT + threadIdx.x; e < n12; e += (size_t)gridDim.x * kNT) {
+    const double2 rv = r[base + e];
+    double2 pv = p[base + e];
+    pv.x = fma(bt, pv.x, rv.x);
+    pv.y = fma(bt, pv.y, rv.y);
+    p[base + e] = pv;
+  }
+}
+
+// d = b - a (residual b - D x)
+__global__ void __launch_bounds__(kNT) sub_kernel(const double2* __restrict__ b, const double2* __restrict__ a,
+                                                  double2* __restrict__ d, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)kNT + threadIdx.x; t < n; t += (size_t)gridDim.x * kNT)
+    d[t] = make_double2(b[t].x - a[t].x, b[t].y - a[t].y);
+}
+
+struct CgCtx {
+  ov_ctx* ctx;
+  double m_q;
+  int nrhs;
+  size_t n12;
+  ov_solve_opts o;
+  cudaStream_t s;
+  double2* t1;  // gamma5 scratch
+  double2* t2;
+  double* part;  // [nrhs][kDotBlocks] device partials
+  std::vector<double> hpart;
+  SolveOut acc;  // accumulated inner-solve statistics
+  int applies = 0;
+};
+
+void add_inner(CgCtx& c, const SolveOut& so) {
+  c.acc.inner_iterations += so.iterations;
+  c.acc.node_updates += so.node_updates;
+  c.acc.launches += so.launches;
+  c.acc.error_bound = std::max(c.acc.error_bound, so.error_bound);
+  c.applies += 1;
+}
+
+// out = D_ov(m_q) in (canonical layout, all sources)
+int apply_D(CgCtx& c, const double2* in, double2* out) {
+  SolveOut so;
+  double2* s_soa = nullptr;
+  const int st = sign_core(c.ctx, in, c.nrhs, c.o, &so, c.s, &s_soa, nullptr);
+  if (st != OV_OK) return st;  // an inner solve that misses its tolerance stops the outer one
+  add_inner(c, so);
+  return launch_overlap_epilogue(c.ctx, in, s_soa, out, c.m_q, c.nrhs, c.s);
+}
+
+// out = D^dag in = gamma5 D gamma5 in
+int apply_Ddag(CgCtx& c, const double2* in, double2* out) {
+  int st = launch_gamma5_aos(c.ctx, in, c.t1, c.nrhs, c.s);
+  if (st == OV_OK) st = apply_D(c, c.t1, c.t2);
+  if (st == OV_OK) st = launch_gamma5_aos(c.ctx, c.t2, out, c.nrhs, c.s);
+  return st;
+}
+
+// per-source sums of the partials written by the last dot/update launch (fixed order)
+int read_sums(CgCtx& c, std::vector<double>& out) {
+  cudaError_t e = cudaMemcpyAsync(c.hpart.data(), c.part, sizeof(double) * c.hpart.size(), cudaMemcpyDeviceToHost, c.s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.s);
+  if (e != cudaSuccess) return ctx_cuda(c.ctx, e, "read partial sums");
+  out.assign(c.nrhs, 0.0);
+  for (int r = 0; r < c.nrhs; ++r)
+    for (int k = 0; k < kDotBlocks; ++k) out[r] += c.hpart[(size_t)r * kDotBlocks + k];
+  return OV_OK;
+}
+
+int dot(CgCtx& c, const double2* u, const double2* v, std::vector<double>& out) {
+  cg_dot_kernel<<<dim3(kDotBlocks, c.nrhs), kNT, 0, c.s>>>(u, v, c.part, c.n12);
+  OV_CHECK_LAUNCH(c.ctx, "cg_dot_kernel");
+  return read_sums(c, out);
+}
+
+}  // namespace
+
+extern "C" int ov_overlap_solve(ov_ctx* ctx, double m_q, const void* b, void* x, int nrhs, const ov_solve_opts* inner,
+                                double tol, int max_iter, ov_stats* stats, void* stream) {
+  const double t0 = now_ms();
+  if (!ctx) return OV_ERR_INVALID_ARG;
+  if (!ctx->have_gauge) return ctx_fail(ctx, OV_ERR_NO_GAUGE, "ov_set_gauge has not been called");
+  if (!ctx->have_contour) return ctx_fail(ctx, OV_ERR_NO_CONTOUR, "no contour set");
+  if (nrhs < 0 || (nrhs > 0 && (!b || !x)) || b == x) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "bad vectors");
+  if (!std::isfinite(m_q)) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "m_q is not finite");
+  if (!(tol > 0.0) || !(tol < 1.0)) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "tol must be in (0, 1)");
+  if (max_iter < 1) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "max_iter must be >= 1");
+  ov_solve_opts o = resolve_opts(inner);
+  int st = check_opts(ctx, o);
+  if (st != OV_OK) return st;
+  if (nrhs == 0) return OV_OK;
+  DeviceGuard dg(ctx->device);
+  CgCtx c;
+  c.ctx = ctx;
+  c.m_q = m_q;
+  c.nrhs = nrhs;
+  c.n12 = (size_t)12 * ctx->g.V;
+  c.s = (cudaStream_t)stream;
+  const bool host_io = o.host_io != 0;
+  o.host_io = 0;  // the applies below work on device buffers
+  c.o = o;
+  const size_t n = c.n12 * nrhs, bytes = sizeof(double2) * n;
+  const double2* bd = stage_in(ctx, b, bytes, host_io ? 1 : 0, "cg.b", c.s, &st);
+  double2* xd = host_io ? (double2*)ws_get(ctx, "cg.x", bytes, &st) : (double2*)x;
+  double2* r = (double2*)ws_get(ctx, "cg.r", bytes, &st);
+  double2* p = (double2*)ws_get(ctx, "cg.p", bytes, &st);
+  double2* q = (double2*)ws_get(ctx, "cg.q", bytes, &st);
+  double2* w = (double2*)ws_get(ctx, "cg.w", bytes, &st);  // D p
+  c.t1 = (double2*)ws_get(ctx, "cg.t1", bytes, &st);
+  c.t2 = (double2*)ws_get(ctx, "cg.t2", bytes, &st);
+  c.part = (double*)ws_get(ctx, "cg.part", sizeof(double) * kDotBlocks * nrhs, &st);
+  if (st != OV_OK) return st;
+  c.hpart.resize((size_t)kDotBlocks * nrhs);
+  double* coef = (double*)ws_get(ctx, "cg.coef", sizeof(double) * nrhs, &st);
+  if (st != OV_OK) return st;
+
+  // x = 0, r = p = D^dag b
+  cudaError_t e = cudaMemsetAsync(xd, 0, bytes, c.s);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "clear x");
+  if ((st = apply_Ddag(c, bd, r)) != OV_OK) return st;
+  e = cudaMemcpyAsync(p, r, bytes, cudaMemcpyDeviceToDevice, c.s);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy r");
+  std::vector<double> rr, rr0, ww, coef_h(nrhs), rr_new;
+  if ((st = dot(c, r, r, rr)) != OV_OK) return st;
+  rr0 = rr;
+  std::vector<int> done(nrhs, 0);
+  for (int k = 0; k < nrhs; ++k) done[k] = !(rr0[k] > 0.0);  // zero source: x = 0
+  int iters = 0, ndone = 0;
+  for (int k = 0; k < nrhs; ++k) ndone += done[k];
+  while (ndone < nrhs && iters < max_iter) {
+    ++iters;
+    // q = D^dag D p;  alpha = ||r||^2 / ||D p||^2
+    if ((st = apply_D(c, p, w)) != OV_OK) return st;
+    if ((st = apply_Ddag(c, w, q)) != OV_OK) return st;
+    if ((st = dot(c, w, w, ww)) != OV_OK) return st;
+    for (int k = 0; k < nrhs; ++k) {
+      coef_h[k] = (done[k] || !(ww[k] > 0.0)) ? 0.0 : rr[k] / ww[k];
+      if (!std::isfinite(coef_h[k])) return ctx_fail(ctx, OV_ERR_BREAKDOWN, "non-finite CG step");
+    }
+    e = cudaMemcpyAsync(coef, coef_h.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c.s);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy alpha");
+    cg_xr_kernel<<<dim3(kDotBlocks, nrhs), kNT, 0, c.s>>>(xd, r, p, q, coef, c.part, c.n12);
+    OV_CHECK_LAUNCH(ctx, "cg_xr_kernel");
+    if ((st = read_sums(c, rr_new)) != OV_OK) return st;
+    for (int k = 0; k < nrhs; ++k) {
+      if (done[k]) {
+        coef_h[k] = 0.0;
+        continue;
+      }
+      if (std::sqrt(rr_new[k]) <= tol * std::sqrt(rr0[k])) {
+        done[k] = 1;
+        ++ndone;
+      }
+      coef_h[k] = rr_new[k] / rr[k];
+      rr[k] = rr_new[k];
+    }
+    if (ndone == nrhs) break;
+    e = cudaMemcpyAsync(coef, coef_h.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, c.s);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy beta");
+    cg_p_kernel<<<dim3(kDotBlocks, nrhs), kNT, 0, c.s>>>(p, r, coef, c.n12);
+    OV_CHECK_LAUNCH(ctx, "cg_p_kernel");
+  }
+  // true residual ||b - D x|| / ||b|| per source
+  if ((st = apply_D(c, xd, w)) != OV_OK) return st;
+  sub_kernel<<<152 * 8, kNT, 0, c.s>>>(bd, w, q, n);
+  OV_CHECK_LAUNCH(ctx, "sub_kernel");
+  std::vector<double> res2, bb;
+  if ((st = dot(c, q, q, res2)) != OV_OK) return st;
+  if ((st = dot(c, bd, bd, bb)) != OV_OK) return st;
+  double worst = 0.0, worst_ne = 0.0;
+  for (int k = 0; k < nrhs; ++k) {
+    if (bb[k] > 0.0) worst = std::max(worst, std::sqrt(res2[k] / bb[k]));
+    if (rr0[k] > 0.0) worst_ne = std::max(worst_ne, std::sqrt(rr[k] / rr0[k]));
+  }
+  if (host_io) {
+    e = cudaMemcpyAsync(x, xd, bytes, cudaMemcpyDeviceToHost, c.s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.s);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "device-to-host copy");
+  }
+  SolveOut so = c.acc;
+  so.iterations = iters;
+  so.refine_rounds = c.applies;
+  so.converged = (ndone == nrhs) ? 1 : 0;
+  so.max_residual = worst;
+  so.error_bound = worst_ne;
+  kt_collect(ctx);
+  fill_stats(stats, so, now_ms() - t0);
+  return so.converged ? OV_OK : ctx_fail(ctx, OV_ERR_NOT_CONVERGED, "overlap CG did not reach tol in max_iter");
+}

@@ -36,7 +36,7 @@ EXPORTS = (
     "ov_create", "ov_destroy", "ov_last_error", "ov_set_gauge", "ov_apply_HW", "ov_set_contour",
     "ov_set_contour_ellipse", "ov_get_contour", "ov_place_contour", "ov_sgn_HW_apply", "ov_overlap_apply",
     "ov_sgn_vjp", "ov_overlap_vjp", "ov_set_kernel_timing", "ov_kernel_times", "ov_version",
-    "ov_apply_HW_noalloc", "ov_set_hw32_variant", "ov_hw32_variants", "ov_set_persistent",
+    "ov_apply_HW_noalloc", "ov_set_hw32_variant", "ov_hw32_variants", "ov_set_persistent", "ov_overlap_solve",
 )
 
 
@@ -91,6 +91,7 @@ def _load():
         "ov_set_hw32_variant": [vp, i],
         "ov_set_persistent": [vp, i],
         "ov_hw32_variants": [i, ip, ip, ip],
+        "ov_overlap_solve": [vp, d, vp, vp, i, ctypes.POINTER(SolveOpts), d, i, ctypes.POINTER(Stats), vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -223,6 +224,20 @@ class Context:
         stream_p = None if o.host_io and stream is None else _stream_ptr(stream)
         rc = _lib.ov_overlap_apply(self._h, float(m_q), _ptr(b), _ptr(out), int(nrhs), ctypes.byref(o),
                                    ctypes.byref(st), stream_p)
+        self._check(rc, (OV_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        d = st.as_dict()
+        d["status"] = rc
+        return d
+
+    def overlap_solve(self, m_q, b, x, nrhs, inner=None, tol=1e-10, max_iter=10000, stream=None,
+                      allow_not_converged=False):
+        """x = D_ov(m_q)^-1 b for nrhs sources (CG on the normal equations; see ov_overlap_solve).
+        Returns the stats: iterations = CG iterations, max_residual = true ||b - D x|| / ||b||."""
+        st = Stats()
+        o = inner if inner is not None else self.opts()
+        stream_p = None if o.host_io and stream is None else _stream_ptr(stream)
+        rc = _lib.ov_overlap_solve(self._h, float(m_q), _ptr(b), _ptr(x), int(nrhs), ctypes.byref(o), float(tol),
+                                   int(max_iter), ctypes.byref(st), stream_p)
         self._check(rc, (OV_ERR_NOT_CONVERGED,) if allow_not_converged else ())
         d = st.as_dict()
         d["status"] = rc
