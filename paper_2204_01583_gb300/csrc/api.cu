@@ -233,6 +233,8 @@ int ov_destroy(ov_ctx* ctx) {
   }
   for (auto e : ctx->event_pool) cudaEventDestroy(e);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  for (auto st : ctx->aux_streams) cudaStreamDestroy(st);
+  for (auto e : ctx->cap_events) cudaEventDestroy(e);
   if (ctx->host_flag) cudaFreeHost(ctx->host_flag);
   delete ctx;
   return OV_OK;
@@ -679,6 +681,13 @@ int ov_hw32_variants(int k, int* rhs_tile, int* compressed, int* threads) {
     *threads = 128;
   }
   return n + 3;
+}
+
+int ov_set_concurrency(ov_ctx* ctx, int groups) {
+  if (!ctx) return OV_ERR_INVALID_ARG;
+  if (groups < 0 || groups > 64) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "groups must be in [0, 64]");
+  ctx->groups = groups;
+  return OV_OK;
 }
 
 int ov_set_persistent(ov_ctx* ctx, int enable) {

@@ -86,6 +86,7 @@ struct ov_ctx {
   std::map<int, int> hw32_choice;      // nrhs -> autotuned FP32 stencil variant
   int hw32_force = -1;                 // ov_set_hw32_variant
   bool no_coop = true;                 // ov_set_persistent(ctx, 1) enables the persistent loop
+  int groups = 0;                      // ov_set_concurrency: source groups per graph (0 = auto)
 
   // quadrature S_N = c0 + sum_j c_j (z_j - H)^-1
   std::vector<double2> z, c;
@@ -96,6 +97,8 @@ struct ov_ctx {
   std::map<std::string, DevBuf> bufs;
   int* host_flag = nullptr;  // pinned host word for convergence reads
   cudaStream_t cap_stream = nullptr;
+  std::vector<cudaStream_t> aux_streams;  // extra capture branches (source groups)
+  std::vector<cudaEvent_t> cap_events;    // fork/join events of those branches
   std::map<GraphKey, cudaGraphExec_t> graphs;
 
   // kernel timing

@@ -957,8 +957,93 @@ struct SolveWs {
   SolveArgs<R> a{};
   int nblk1 = 0, nblk2 = 0, nblk2u = 0;
   int nslots = 3;
+  int nshift = 0;
+  int max_iter = 0;  // row length of the per-source histories
   SolveParams* prm_dev = nullptr;
 };
+
+// The arguments of sources r0, r0 + 1, ... as a launch of their own sees them: every
+// per-source array offset by r0 (kernels index sources by blockIdx.y).
+template <typename R>
+SolveArgs<R> args_for_sources(const SolveWs<R>& w, int r0) {
+  SolveArgs<R> a = w.a;
+  const size_t n12 = (size_t)12 * w.a.g.V, ns = (size_t)w.nshift, r = (size_t)r0;
+  a.ring += r * w.nslots * n12;
+  if (a.p) a.p += r * ns * n12;
+  if (a.x) a.x += r * ns * n12;
+  if (a.sacc) a.sacc += r * n12;
+  if (a.ssum) a.ssum += r * n12;
+  if (a.stencil) a.stencil += r * n12;
+  a.src += r;
+  a.sh += r * ns;
+  a.z += r * ns;
+  a.c += r * ns;
+  a.act_idx += r * ns;
+  a.act_l += r * ns;
+  a.act_cz += r * ns;
+  a.act_z += r * ns;
+  a.part1 += r * w.nblk1;
+  a.part2 += r * w.nblk2u;
+  a.cnt += 2 * r;
+  if (a.hist_a) a.hist_a += r * w.max_iter;
+  if (a.hist_b) a.hist_b += r * w.max_iter;
+  if (a.gco) a.gco += r * w.max_iter;
+  if (a.rrec) a.rrec += r * w.max_iter;
+  if (a.tol_src) a.tol_src += r;
+  return a;
+}
+
+// Source groups of a replayed graph.  Sources are independent, so the per-iteration
+// kernels of G groups can run as parallel branches of one graph: on small lattices, where
+// a launch leaves SMs idle through its tail, its serial last-block step and the next
+// launch's ramp, each branch fills the other's gaps.  Auto: two groups when the stencil
+// grid of all sources fits two waves (152 SMs x 4 blocks) and there are >= 2 sources.
+int source_groups(const ov_ctx* ctx, int nsrc, int nblk1) {
+  int g = ctx->groups;
+  if (g <= 0) g = (nsrc >= 2 && (size_t)nblk1 * nsrc <= (size_t)2 * 152 * 4) ? 2 : 1;
+  return std::max(1, std::min(g, nsrc));
+}
+
+// Capture body(stream, args, sources) once per source group, each group on its own branch
+// (forked from and joined back to the capture stream), and instantiate the graph.
+template <typename R, typename F>
+int capture_groups(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, int G, F body, cudaGraphExec_t* exec) {
+  while ((int)ctx->aux_streams.size() < G) {
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaStreamCreate");
+    ctx->aux_streams.push_back(st);
+  }
+  while ((int)ctx->cap_events.size() < G) {
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaEventCreate");
+    ctx->cap_events.push_back(ev);
+  }
+  cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaStreamBeginCapture");
+  if (G > 1) {
+    cudaEventRecord(ctx->cap_events[0], ctx->cap_stream);
+    for (int g = 1; g < G; ++g) cudaStreamWaitEvent(ctx->aux_streams[g], ctx->cap_events[0], 0);
+  }
+  for (int g = 0; g < G; ++g) {
+    const int lo = (int)((long long)nsrc * g / G), hi = (int)((long long)nsrc * (g + 1) / G);
+    body(g == 0 ? ctx->cap_stream : ctx->aux_streams[g], args_for_sources(w, lo), hi - lo);
+  }
+  if (G > 1) {
+    for (int g = 1; g < G; ++g) {
+      cudaEventRecord(ctx->cap_events[g], ctx->aux_streams[g]);
+      cudaStreamWaitEvent(ctx->cap_stream, ctx->cap_events[g], 0);
+    }
+  }
+  cudaGraph_t gph = nullptr;
+  e = cudaStreamEndCapture(ctx->cap_stream, &gph);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(exec, gph, 0);
+  cudaGraphDestroy(gph);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaGraphInstantiate");
+  return OV_OK;
+}
 
 template <typename R>
 int setup_ws(ov_ctx* ctx, int nsrc, int ns, bool want_x, bool want_sacc, bool want_hist, int max_iter,
@@ -969,6 +1054,8 @@ int setup_ws(ov_ctx* ctx, int nsrc, int ns, bool want_x, bool want_sacc, bool wa
   int st = OV_OK;
   std::string t(tag);
   w->nblk1 = (V + kSplitSites - 1) / kSplitSites;
+  w->nshift = ns;
+  w->max_iter = max_iter;
   // the init kernel uses the K2 partial buffer with up to ceil(12V / NT2) blocks
   w->nblk2 = (int)((n12 + NT2 - 1) / NT2);
   // K2 is a grid-stride loop: about two blocks per SM in total when the vectors are small
@@ -1032,26 +1119,25 @@ int run_iterations(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, int nshift, int f
   const bool graph = o.use_graph && !ctx->timing;
   cudaGraphExec_t exec = nullptr;
   if (graph) {
+    const int G = source_groups(ctx, nsrc, w.nblk1);
     GraphKey key{{(const void*)w.a.ring, (const void*)w.a.p, (const void*)w.a.x, (const void*)w.a.sacc},
-                 nsrc, nshift, flavour, chunk};
+                 nsrc, nshift, flavour * 128 + G, chunk};
     auto it = ctx->graphs.find(key);
     if (it != ctx->graphs.end()) {
       exec = it->second;
     } else {
       // the graph replays identical launches: every argument is a workspace pointer
       // and all per-iteration state lives in device memory
-      cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
-      if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaStreamBeginCapture");
-      for (int k = 0; k < chunk; ++k) {
-        lanczos_hw_kernel<R><<<dim3(w.nblk1, nsrc), NT1, 0, ctx->cap_stream>>>(w.a);
-        lanczos_update_kernel<R><<<dim3(w.nblk2u, nsrc), NT2, 0, ctx->cap_stream>>>(w.a);
-      }
-      cudaGraph_t gph = nullptr;
-      e = cudaStreamEndCapture(ctx->cap_stream, &gph);
-      if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaStreamEndCapture");
-      e = cudaGraphInstantiate(&exec, gph, 0);
-      cudaGraphDestroy(gph);
-      if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaGraphInstantiate");
+      const int st = capture_groups<R>(
+          ctx, w, nsrc, G,
+          [&](cudaStream_t cs, const SolveArgs<R>& a, int n) {
+            for (int k = 0; k < chunk; ++k) {
+              lanczos_hw_kernel<R><<<dim3(w.nblk1, n), NT1, 0, cs>>>(a);
+              lanczos_update_kernel<R><<<dim3(w.nblk2u, n), NT2, 0, cs>>>(a);
+            }
+          },
+          &exec);
+      if (st != OV_OK) return st;
       ctx->graphs[key] = exec;
     }
   }
@@ -1425,22 +1511,20 @@ static int solve_sign_coef(ov_ctx* ctx, const double2* b_soa, double2* out_soa, 
   const bool graph = o.use_graph && !ctx->timing;
   cudaGraphExec_t exec = nullptr;
   if (graph && kmax >= chunk) {
+    const int G = source_groups(ctx, nsrc, w.nblk1);
     GraphKey key{{(const void*)w.a.ring, (const void*)gco, (const void*)w.a.sacc, (const void*)w.a.hist_a},
-                 nsrc, ns, 3, chunk};
+                 nsrc, ns, 3 * 128 + G, chunk};
     auto it = ctx->graphs.find(key);
     if (it != ctx->graphs.end()) {
       exec = it->second;
     } else {
-      cudaError_t ce = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
-      if (ce != cudaSuccess) return ctx_cuda(ctx, ce, "cudaStreamBeginCapture");
-      for (int k = 0; k < chunk; ++k)
-        lanczos_regen_kernel<R><<<dim3(w.nblk1, nsrc), NT1, 0, ctx->cap_stream>>>(w.a);
-      cudaGraph_t gph = nullptr;
-      ce = cudaStreamEndCapture(ctx->cap_stream, &gph);
-      if (ce != cudaSuccess) return ctx_cuda(ctx, ce, "cudaStreamEndCapture");
-      ce = cudaGraphInstantiate(&exec, gph, 0);
-      cudaGraphDestroy(gph);
-      if (ce != cudaSuccess) return ctx_cuda(ctx, ce, "cudaGraphInstantiate");
+      st = capture_groups<R>(
+          ctx, w, nsrc, G,
+          [&](cudaStream_t cs, const SolveArgs<R>& a, int n) {
+            for (int k = 0; k < chunk; ++k) lanczos_regen_kernel<R><<<dim3(w.nblk1, n), NT1, 0, cs>>>(a);
+          },
+          &exec);
+      if (st != OV_OK) return st;
       ctx->graphs[key] = exec;
     }
   }

@@ -37,6 +37,7 @@ EXPORTS = (
     "ov_set_contour_ellipse", "ov_get_contour", "ov_place_contour", "ov_sgn_HW_apply", "ov_overlap_apply",
     "ov_sgn_vjp", "ov_overlap_vjp", "ov_set_kernel_timing", "ov_kernel_times", "ov_version",
     "ov_apply_HW_noalloc", "ov_set_hw32_variant", "ov_hw32_variants", "ov_set_persistent", "ov_overlap_solve",
+    "ov_set_concurrency",
 )
 
 
@@ -90,6 +91,7 @@ def _load():
         "ov_apply_HW_noalloc": [ip, i, d, vp, vp, vp, i, vp],
         "ov_set_hw32_variant": [vp, i],
         "ov_set_persistent": [vp, i],
+        "ov_set_concurrency": [vp, i],
         "ov_hw32_variants": [i, ip, ip, ip],
         "ov_overlap_solve": [vp, d, vp, vp, i, ctypes.POINTER(SolveOpts), d, i, ctypes.POINTER(Stats), vp],
     }
@@ -268,6 +270,10 @@ class Context:
         self._check(_lib.ov_set_hw32_variant(self._h, int(k)))
 
     # ------------------------------------------------------------------ timing
+    def set_concurrency(self, groups=0):
+        """Parallel graph branches over groups of sources (0 = automatic)."""
+        self._check(_lib.ov_set_concurrency(self._h, int(groups)))
+
     def set_kernel_timing(self, enable=True):
         self._check(_lib.ov_set_kernel_timing(self._h, int(bool(enable))))
 

@@ -228,3 +228,17 @@ def test_persistent_and_per_iteration_launches_agree(gpu_lib, config2):
     for k in range(4):
         assert rel(a[k], c[k]) < 1e-11
     assert rel(a[0], want0) < 1e-10
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp64_2pass", "fp64_regen", "f32x2"])
+def test_source_groups_give_identical_results(gpu_lib, config2, mode):
+    """Replaying the per-iteration kernels as 1, 2 or 4 parallel graph branches over the
+    sources changes no arithmetic: bitwise identical results and iteration counts."""
+    ctx, U, b, spec, want0 = config2
+    outs = []
+    for groups in (1, 2, 4):
+        ctx.set_concurrency(groups)
+        outs.append(sgn_gpu(ctx, b, nrhs=4, tol=1e-12, mode=mode))
+    ctx.set_concurrency(0)
+    for o, st in outs[1:]:
+        assert np.array_equal(o, outs[0][0]) and st["iterations"] == outs[0][1]["iterations"]
