@@ -85,6 +85,10 @@ def parse():
     ap.add_argument("--variant", type=int, default=None, help="dslash workloads: time only this FP32 stencil variant")
     ap.add_argument("--compare-steps", type=int, default=2,
                     help="mixed workloads: steps of each plain FP64 form timed for the comparison")
+    ap.add_argument("--nsrc", type=int, default=None, help="use only the first N sources (profiling cases)")
+    ap.add_argument("--max-iter", type=int, default=None,
+                    help="cap the Krylov iterations (profiling cases; the line is then not a valid measurement)")
+    ap.add_argument("--concurrency", type=int, default=0, help="source groups replayed as parallel graph branches")
     return ap.parse_args()
 
 
@@ -218,13 +222,18 @@ def run_reference(args, wl):
 
 
 def config_dict(args, wl, mode):
-    return {
+    c = {
         "workload": args.workload, "lattice": "x".join(map(str, wl["dims"])), "link_eps": wl["eps"], "m0": M0,
-        "r": 1.0, "bc_t": "antiperiodic", "m_q": wl["m_q"], "N_q": wl["n_q"], "sources_per_gpu": wl["nsrc"],
+        "r": 1.0, "bc_t": "antiperiodic", "m_q": wl["m_q"], "N_q": wl["n_q"],
+        "sources_per_gpu": args.nsrc or wl["nsrc"],
         "source": "complex Gaussian" if wl["src"] == "gauss" else "spin-colour point sources",
         "tol": wl["tol"], "mode": mode, "contour": "single ellipse placed from Lanczos bounds (setup, untimed)",
         "l2": "256 MiB buffer written between timed steps", "parallelism": f"independent sources per GPU x{args.gpus}",
+        "graph_branches": args.concurrency or "auto",
     }
+    if args.max_iter is not None:
+        c["profiling_case"] = f"Krylov iterations capped at {args.max_iter}: not a measurement of the workload"
+    return c
 
 
 # ------------------------------------------------------------------ ours
@@ -275,6 +284,8 @@ def run_ours(args, wl):
 
     mode = args.mode or wl["mode"]
     U, b = workload_inputs(wl, rank)
+    if args.nsrc:
+        b = b[: args.nsrc]
     nsrc = b.shape[0]
     dev = torch.device("cuda", local)
     ctx = lib.Context(wl["dims"], bc_t=-1, m0=M0, device=local)
@@ -282,12 +293,14 @@ def run_ours(args, wl):
     spec = ctx.place_contour(wl["n_q"], steps=150)
     bd = torch.from_numpy(b).to(dev)
     out = torch.empty_like(bd)
-    opts = ctx.opts(mode=mode, tol=wl["tol"])
+    capped = args.max_iter is not None
+    opts = ctx.opts(mode=mode, tol=wl["tol"], max_iter=args.max_iter or 20000)
+    ctx.set_concurrency(args.concurrency)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(o=opts, src=bd, dst=out):
-        return ctx.overlap(wl["m_q"], src, dst, nsrc, o)
+        return ctx.overlap(wl["m_q"], src, dst, nsrc, o, allow_not_converged=capped)
 
     def barrier():
         if world > 1:
@@ -328,7 +341,7 @@ def run_ours(args, wl):
     if not args.no_e2e:
         hb = torch.from_numpy(b).pin_memory()
         ho = torch.empty_like(hb).pin_memory()
-        ho_opts = ctx.opts(mode=mode, tol=wl["tol"], host_io=True)
+        ho_opts = ctx.opts(mode=mode, tol=wl["tol"], host_io=True, max_iter=args.max_iter or 20000)
         step(ho_opts, hb, ho)
         barrier()
         te = []
@@ -337,7 +350,7 @@ def run_ours(args, wl):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ctx.overlap(wl["m_q"], hb, ho, nsrc, ho_opts, stream=stream)
+            ctx.overlap(wl["m_q"], hb, ho, nsrc, ho_opts, stream=stream, allow_not_converged=capped)
             e1.record(stream)
             e1.synchronize()
             te.append(e0.elapsed_time(e1))
@@ -373,7 +386,7 @@ def run_ours(args, wl):
                    "error_bound": stats[-1]["error_bound"], "converged": stats[-1]["converged"],
                    "spectrum": spec},
     }
-    if mode in ("mixed", "f32x2") and args.compare_steps > 0:
+    if mode in ("mixed", "f32x2") and args.compare_steps > 0 and not capped:
         line[f"{mode}_vs_fp64"] = compare_fp64(ctx, wl, bd, out, nsrc, stream, flush, args.compare_steps,
                                              total_ms / args.steps)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

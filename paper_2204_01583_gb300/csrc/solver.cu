@@ -1141,18 +1141,20 @@ int run_iterations(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, int nshift, int f
       ctx->graphs[key] = exec;
     }
   }
+  const int G = graph ? source_groups(ctx, nsrc, w.nblk1) : 1;
   int done_iters = 0;
   while (done_iters < max_iter) {
     const int n = std::min(chunk, max_iter - done_iters);
     if (graph && n == chunk) {
       cudaError_t e = cudaGraphLaunch(exec, s);
       if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaGraphLaunch");
+      *launches += 2.0 * n * G;
     } else {
       for (int k = 0; k < n; ++k) launch_iteration<R>(ctx, w, nsrc, s);
       OV_CHECK_LAUNCH(ctx, "lanczos kernels");
+      *launches += 2.0 * n;
     }
     done_iters += n;
-    *launches += 2.0 * n;
     cudaError_t e = cudaMemcpyAsync(ctx->host_flag, w.a.done_count, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaMemcpyAsync(done)");
     e = cudaStreamSynchronize(s);
@@ -1528,12 +1530,14 @@ static int solve_sign_coef(ov_ctx* ctx, const double2* b_soa, double2* out_soa, 
       ctx->graphs[key] = exec;
     }
   }
+  const int Gr = exec ? source_groups(ctx, nsrc, w.nblk1) : 1;
   int done = 0;
   while (done < kmax) {
     const int n = std::min(chunk, kmax - done);
     if (exec && n == chunk) {
       e = cudaGraphLaunch(exec, s);
       if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaGraphLaunch");
+      launches += (double)n * (Gr - 1);  // the other branches' launches
     } else {
       for (int k = 0; k < n; ++k) {
         cudaEvent_t ev;
