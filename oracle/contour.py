@@ -55,3 +55,41 @@ def rational(lam, z, c, c0):
     """r_N(lambda) = c0 + sum_j c_j / (z_j - lambda), the value of S_N on an eigenvalue."""
     lam = np.asarray(lam, dtype=np.complex128)
     return c0 + np.sum(c[None, :] / (z[None, :] - lam.reshape(-1, 1)), axis=1).reshape(lam.shape)
+
+
+def zolotarev(n_poles: int, lam_min: float, lam_max: float, samples: int = 400001):
+    """Zolotarev's optimal uniform rational approximation of sgn(lambda) on
+    [-lam_max, -lam_min] u [lam_min, lam_max], written as a resolvent sum (z, c, c0 = 0).
+
+    Not in the paper (which names better contour rules as future work in its
+    "Summary"); this is the classical construction.  With x = lambda / lam_min,
+    b = lam_max / lam_min, parameter m' = 1 - 1/b^2, K' = K(m'), and
+    c_l = sn^2(l K' / 2n | m') / cn^2(l K' / 2n | m'), l = 1 .. 2n - 1,
+
+        R(x) = d0 x prod_{i=1}^{n-1} (x^2 + c_{2i}) / prod_{i=1}^{n} (x^2 + c_{2i-1})
+             = x sum_{l=1}^{n} b_l / (x^2 + c_{2l-1}),
+
+    with d0 set so that R - 1 equioscillates between -delta and +delta on [1, b] (found
+    here by dense sampling in log x).  Since lam / (lam^2 + s^2) =
+    -1/2 [1 / (i s - lam) + 1 / (-i s - lam)], each pole pair gives the nodes
+    z = +-i s_l, s_l = lam_min sqrt(c_{2l-1}), both with coefficient -b_l lam_min / 2.
+    Returns (z, c, c0, delta), nodes ordered i s_1 .. i s_n, -i s_n .. -i s_1."""
+    from scipy.special import ellipj, ellipk
+
+    n = int(n_poles)
+    b = lam_max / lam_min
+    m1 = 1.0 - 1.0 / b**2
+    K1 = ellipk(m1)
+    sn, cn, _, _ = ellipj(np.arange(1, 2 * n) * K1 / (2 * n), m1)
+    cl = sn**2 / cn**2
+    codd, ceven = cl[0::2], cl[1::2]
+    x = np.geomspace(1.0, b, samples)
+    Rt = x * np.prod(x[:, None] ** 2 + ceven[None, :], axis=1) / np.prod(x[:, None] ** 2 + codd[None, :], axis=1)
+    lo, hi = Rt.min(), Rt.max()
+    d0 = 2.0 / (lo + hi)
+    delta = (hi - lo) / (hi + lo)
+    bl = np.array([d0 * np.prod(ceven - co) / np.prod(np.delete(codd, i) - co) for i, co in enumerate(codd)])
+    s = lam_min * np.sqrt(codd)
+    z = np.concatenate([1j * s, -1j * s[::-1]])
+    c = np.concatenate([-0.5 * lam_min * bl, -0.5 * lam_min * bl[::-1]]).astype(np.complex128)
+    return z.astype(np.complex128), c, 0.0 + 0.0j, float(delta)

@@ -61,3 +61,57 @@ def test_single_contour_is_twice_projector_minus_one():
     zp, p = contour.projector_coefficients(48, 2.0, 2.0, 0.3)
     lam = np.array([-1.0, 0.5, 3.0])
     assert np.allclose(contour.rational(lam, z, c, c0), 2 * contour.rational(lam, zp, p, 0.0) - 1)
+
+
+# ----------------------------------------------------------------- Zolotarev rule
+
+def _extrema(err):
+    """Values of err at its interior local extrema and the two endpoints, in order."""
+    d = np.diff(err)
+    idx = [0] + [k for k in range(1, len(d)) if d[k - 1] * d[k] < 0] + [len(err) - 1]
+    return err[idx]
+
+
+@pytest.mark.parametrize("n,b", [(3, 20.0), (4, 20.0), (5, 100.0)])
+def test_zolotarev_equioscillates(n, b):
+    """The optimal approximation of degree (2n-1, 2n) equioscillates: sgn - r has 2n + 1
+    extrema on [1, b] with alternating signs and equal magnitude delta (Chebyshev)."""
+    z, c, c0, delta = contour.zolotarev(n, 1.0, b)
+    lam = np.geomspace(1.0, b, 200001)
+    err = contour.rational(lam, z, c, c0).real - 1.0
+    ext = _extrema(err)
+    assert len(ext) == 2 * n + 1
+    assert np.all(np.sign(ext[1:]) == -np.sign(ext[:-1]))
+    assert np.allclose(np.abs(ext), delta, rtol=1e-6)
+    assert np.abs(err).max() <= delta * (1 + 1e-6)
+
+
+def test_zolotarev_is_odd_real_and_converges():
+    deltas = []
+    for n in (4, 8, 12):
+        z, c, c0, delta = contour.zolotarev(n, 0.3, 6.0)
+        lam = np.concatenate([np.geomspace(0.3, 6.0, 2001), -np.geomspace(0.3, 6.0, 2001)])
+        r = contour.rational(lam, z, c, c0)
+        assert np.abs(r.imag).max() <= 1e-13
+        assert np.abs(r[:2001] + r[2001:]).max() <= 1e-13  # odd
+        assert np.abs(r.real - np.sign(lam)).max() <= delta * (1 + 1e-6) + 1e-15  # + rounding of the sum
+        deltas.append(delta)
+    # geometric convergence in the number of poles (the rate is set by b = 20)
+    assert deltas[1] < 1e-3 * deltas[0] and deltas[2] < 1e-3 * deltas[1]
+
+
+def test_zolotarev_beats_trapezoid_on_spectrum():
+    """On the spectrum of a small H_W (dense eigvalsh), 12 pole pairs (24 nodes) from the
+    true spectral bounds approximate sgn within delta, far below a 64-node ellipse."""
+    import synthetic as S
+    from oracle import wilson
+
+    U = S.su3_links((2, 2, 2, 4), 0.5, 811)
+    lam = np.linalg.eigvalsh(wilson.dense_HW(U, 1.6))
+    a, b = np.abs(lam).min(), np.abs(lam).max()
+    z, c, c0, delta = contour.zolotarev(12, a, b)
+    err = np.abs(contour.rational(lam, z, c, c0).real - np.sign(lam)).max()
+    assert err <= delta * (1 + 1e-6) + 1e-15
+    ze, ce, c0e = contour.single_contour(64, 0.525 * b, 0.525 * b, 0.3)
+    err_e = np.abs(contour.rational(lam, ze, ce, c0e).real - np.sign(lam)).max()
+    assert err < 1e-3 * err_e
