@@ -179,6 +179,24 @@ int ov_get_contour(const ov_ctx* ctx, int* n, double* z, double* c, double* c0);
  * bound of the spectrum; alpha minimises the predicted method error.  `out` may be NULL. */
 int ov_place_contour(ov_ctx* ctx, int n_q, int steps, ov_spectrum* out, void* stream);
 
+/* Zolotarev node set (not in the paper, whose Summary leaves better quadrature rules to
+ * future work): the optimal uniform rational approximation of sgn(lambda) on
+ * [-lambda_max, -lambda_min] u [lambda_min, lambda_max] with n_poles pole pairs, written
+ * as S = sum_j c_j (z_j - H)^-1 (c0 = 0) with 2 n_poles nodes z_j = +-i s_l on the
+ * imaginary axis, ordered i s_1 .. i s_n, -i s_n .. -i s_1.  Built on the host from Jacobi
+ * elliptic functions; *delta (may be NULL) receives the maximum error on the interval.
+ * ov_zolotarev_rule needs no context or GPU: z, c receive 2 n_poles complex numbers
+ * (interleaved re, im).  Errors: OV_ERR_INVALID_ARG unless 1 <= n_poles <= 128 and
+ * 0 < lambda_min < lambda_max. */
+int ov_zolotarev_rule(int n_poles, double lambda_min, double lambda_max, double* z, double* c, double* delta);
+int ov_set_contour_zolotarev(ov_ctx* ctx, int n_poles, double lambda_min, double lambda_max, double* delta);
+
+/* Spectral bounds as in ov_place_contour, then the Zolotarev node set on
+ * [gap_lo, abs_max_bound]: gap_lo is the Lanczos estimate of min |lambda| lowered by the
+ * residual bound of its H_W^2 Ritz value (by at most 20%).  out->gap = gap_lo,
+ * out->predicted_error = delta, out->gamma = rho = alpha = 0. */
+int ov_place_zolotarev(ov_ctx* ctx, int n_poles, int steps, ov_spectrum* out, void* stream);
+
 /* out = S_N b for nrhs sources (complex double, canonical layout). */
 int ov_sgn_HW_apply(ov_ctx* ctx, const void* b, void* out, int nrhs, const ov_solve_opts* opts,
                     ov_stats* stats, void* stream);

@@ -424,25 +424,39 @@ int ov_get_contour(const ov_ctx* ctx, int* n, double* z, double* c, double* c0) 
   return OV_OK;
 }
 
+// Spectral bounds from Lanczos on H and on H^2: extreme Ritz values lo, hi of H, an upper
+// bound amax of |lambda| (Ritz value plus residual bound), the Ritz estimate gap of min
+// |lambda| and gap_lo, a value below it by the residual bound of the H^2 Ritz value
+// (at most 20% below).
+static int spectral_bounds(ov_ctx* ctx, int steps, cudaStream_t s, double* lo, double* hi, double* amax,
+                           double* gap, double* gap_lo, int* nsteps) {
+  std::vector<double> a, b;
+  int st = lanczos_tridiag(ctx, steps, 0, a, b, s);
+  if (st != OV_OK) return st;
+  double rlo, rhi;
+  tridiag_extreme_eigs(a, b, lo, hi, &rlo, &rhi);
+  *amax = std::max(std::fabs(*lo) + rlo, std::fabs(*hi) + rhi);
+  std::vector<double> a2, b2;
+  st = lanczos_tridiag(ctx, steps, 1, a2, b2, s);
+  if (st != OV_OK) return st;
+  double lo2, hi2, rlo2, rhi2;
+  tridiag_extreme_eigs(a2, b2, &lo2, &hi2, &rlo2, &rhi2);
+  *gap = std::max(std::sqrt(std::max(lo2, 0.0)), 1e-6 * *amax);
+  *gap_lo = std::max(std::sqrt(std::max(lo2 - rlo2, 0.64 * lo2)), 1e-6 * *amax);
+  *nsteps = (int)a.size();
+  return OV_OK;
+}
+
 int ov_place_contour(ov_ctx* ctx, int n_q, int steps, ov_spectrum* out, void* stream) {
   if (!ctx) return OV_ERR_INVALID_ARG;
   if (!ctx->have_gauge) return ctx_fail(ctx, OV_ERR_NO_GAUGE, "ov_set_gauge has not been called");
   if (n_q < 2 || steps < 4) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "need n_q >= 2 and steps >= 4");
   DeviceGuard dg(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  std::vector<double> a, b;
-  int st = lanczos_tridiag(ctx, steps, 0, a, b, s);
+  double lo, hi, amax, gap, gap_lo;
+  int nsteps = 0;
+  int st = spectral_bounds(ctx, steps, s, &lo, &hi, &amax, &gap, &gap_lo, &nsteps);
   if (st != OV_OK) return st;
-  double lo, hi, rlo, rhi;
-  tridiag_extreme_eigs(a, b, &lo, &hi, &rlo, &rhi);
-  const double amax = std::max(std::fabs(lo) + rlo, std::fabs(hi) + rhi);
-  std::vector<double> a2, b2;
-  st = lanczos_tridiag(ctx, steps, 1, a2, b2, s);
-  if (st != OV_OK) return st;
-  double lo2, hi2, rlo2, rhi2;
-  tridiag_extreme_eigs(a2, b2, &lo2, &hi2, &rlo2, &rhi2);
-  double gap = std::sqrt(std::max(lo2, 0.0));
-  gap = std::max(gap, 1e-6 * amax);
   // single ellipse from 0 to 1.05 * amax; alpha minimises the predicted method error
   const double R = 1.05 * amax;
   const double gam = 0.5 * R, rho = 0.5 * R;
@@ -478,7 +492,62 @@ int ov_place_contour(ov_ctx* ctx, int n_q, int steps, ov_spectrum* out, void* st
     out->gamma = gam;
     out->rho = rho;
     out->alpha = best_alpha;
-    out->steps = (int)a.size();
+    out->steps = nsteps;
+  }
+  return OV_OK;
+}
+
+int ov_zolotarev_rule(int n_poles, double lambda_min, double lambda_max, double* z, double* c, double* delta) {
+  if (!z || !c) return OV_ERR_INVALID_ARG;
+  std::vector<double2> zz, cc;
+  double2 c0;
+  const int st = zolotarev_rule(n_poles, lambda_min, lambda_max, zz, cc, c0, delta);
+  if (st != OV_OK) return st;
+  for (size_t j = 0; j < zz.size(); ++j) {
+    z[2 * j] = zz[j].x;
+    z[2 * j + 1] = zz[j].y;
+    c[2 * j] = cc[j].x;
+    c[2 * j + 1] = cc[j].y;
+  }
+  return OV_OK;
+}
+
+int ov_set_contour_zolotarev(ov_ctx* ctx, int n_poles, double lambda_min, double lambda_max, double* delta) {
+  if (!ctx) return OV_ERR_INVALID_ARG;
+  std::vector<double2> z, c;
+  double2 c0;
+  if (zolotarev_rule(n_poles, lambda_min, lambda_max, z, c, c0, delta) != OV_OK)
+    return ctx_fail(ctx, OV_ERR_INVALID_ARG, "need 1 <= n_poles <= 128 and 0 < lambda_min < lambda_max");
+  ctx->z = z;
+  ctx->c = c;
+  ctx->c0 = c0;
+  ctx->have_contour = true;
+  return OV_OK;
+}
+
+int ov_place_zolotarev(ov_ctx* ctx, int n_poles, int steps, ov_spectrum* out, void* stream) {
+  if (!ctx) return OV_ERR_INVALID_ARG;
+  if (!ctx->have_gauge) return ctx_fail(ctx, OV_ERR_NO_GAUGE, "ov_set_gauge has not been called");
+  if (n_poles < 1 || n_poles > 128 || steps < 4)
+    return ctx_fail(ctx, OV_ERR_INVALID_ARG, "need 1 <= n_poles <= 128 and steps >= 4");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  double lo, hi, amax, gap, gap_lo, delta = 0.0;
+  int nsteps = 0;
+  int st = spectral_bounds(ctx, steps, s, &lo, &hi, &amax, &gap, &gap_lo, &nsteps);
+  if (st != OV_OK) return st;
+  st = ov_set_contour_zolotarev(ctx, n_poles, gap_lo, amax, &delta);
+  if (st != OV_OK) return st;
+  if (out) {
+    out->lambda_min = lo;
+    out->lambda_max = hi;
+    out->abs_max_bound = amax;
+    out->gap = gap_lo;
+    out->predicted_error = delta;
+    out->gamma = 0.0;
+    out->rho = 0.0;
+    out->alpha = 0.0;
+    out->steps = nsteps;
   }
   return OV_OK;
 }

@@ -39,6 +39,116 @@ double rational_value(double lam, const std::vector<double2>& z, const std::vect
   return re;
 }
 
+// ------------------------------------------------------------ Zolotarev node set
+// Complete elliptic integral K(m) = pi / (2 AGM(1, sqrt(1 - m))) and the Jacobi elliptic
+// functions sn, cn of parameter m by the arithmetic-geometric-mean scheme (descending
+// Landen transformation; Abramowitz & Stegun 16.4 and 17.6), in double precision.
+double ellip_K(double m) {
+  double a = 1.0, b = std::sqrt(1.0 - m);
+  for (int it = 0; it < 64 && std::fabs(a - b) > 1e-16 * a; ++it) {
+    const double an = 0.5 * (a + b);
+    b = std::sqrt(a * b);
+    a = an;
+  }
+  return M_PI / (2.0 * a);
+}
+
+void ellip_sn_cn(double u, double m, double* sn, double* cn) {
+  double a[40], c[40];
+  a[0] = 1.0;
+  double b = std::sqrt(1.0 - m);
+  c[0] = std::sqrt(m);
+  int n = 0;
+  while (n < 38 && std::fabs(c[n]) > 1e-17) {
+    a[n + 1] = 0.5 * (a[n] + b);
+    c[n + 1] = 0.5 * (a[n] - b);
+    b = std::sqrt(a[n] * b);
+    ++n;
+  }
+  double phi = std::ldexp(a[n] * u, n);  // 2^n a_n u
+  for (int k = n; k > 0; --k) {
+    const double q = std::max(-1.0, std::min(1.0, c[k] * std::sin(phi) / a[k]));
+    phi = 0.5 * (phi + std::asin(q));
+  }
+  *sn = std::sin(phi);
+  *cn = std::cos(phi);
+}
+
+// Zolotarev's optimal rational approximation of sgn on [-lmax, -lmin] u [lmin, lmax] as a
+// resolvent sum: with x = lambda / lmin, b = lmax / lmin, m' = 1 - 1/b^2, K' = K(m') and
+// c_l = sn^2 / cn^2 (l K' / 2n | m'), the function
+//   R(x) = d0 x prod_{i<n} (x^2 + c_{2i}) / prod_{i<=n} (x^2 + c_{2i-1}) = x sum_l b_l / (x^2 + c_{2l-1})
+// equioscillates about 1 on [1, b] with amplitude delta for the right d0 (taken from the
+// extreme values of R / d0, located on a log grid and refined by golden-section search).
+// lambda / (lambda^2 + s^2) = -1/2 [1/(is - lambda) + 1/(-is - lambda)], so each pole pair
+// gives nodes +-i s_l, s_l = lmin sqrt(c_{2l-1}), with coefficient -b_l lmin / 2.
+int zolotarev_rule(int n, double lmin, double lmax, std::vector<double2>& z, std::vector<double2>& c, double2& c0,
+                   double* delta) {
+  if (n < 1 || n > 128 || !(lmin > 0.0) || !(lmax > lmin) || !std::isfinite(lmax)) return OV_ERR_INVALID_ARG;
+  const double bb = lmax / lmin, m1 = 1.0 - 1.0 / (bb * bb), K1 = ellip_K(m1);
+  std::vector<double> cl(2 * n);
+  for (int l = 1; l < 2 * n; ++l) {
+    double sn, cn;
+    ellip_sn_cn(l * K1 / (2.0 * n), m1, &sn, &cn);
+    cl[l] = (sn * sn) / (cn * cn);
+  }
+  auto Rt = [&](double x) {  // R / d0
+    double r = x;
+    for (int i = 1; i <= n; ++i) r /= (x * x + cl[2 * i - 1]);
+    for (int i = 1; i < n; ++i) r *= (x * x + cl[2 * i]);
+    return r;
+  };
+  // extreme values of R / d0 on [1, b]: endpoints and refined interior extrema
+  const int M = 400 * n + 400;
+  const double lb = std::log(bb);
+  std::vector<double> v(M + 1);
+  for (int k = 0; k <= M; ++k) v[k] = Rt(std::exp(lb * k / M));
+  double lo = std::min(v[0], v[M]), hi = std::max(v[0], v[M]);
+  for (int k = 1; k < M; ++k) {
+    const bool mx = v[k] >= v[k - 1] && v[k] >= v[k + 1], mn = v[k] <= v[k - 1] && v[k] <= v[k + 1];
+    if (!mx && !mn) continue;
+    const double sg = mx ? 1.0 : -1.0;  // maximise sg * R
+    double ta = lb * (k - 1) / M, tb = lb * (k + 1) / M;
+    const double gr = 0.5 * (std::sqrt(5.0) - 1.0);
+    double t1 = tb - gr * (tb - ta), t2 = ta + gr * (tb - ta);
+    double f1 = sg * Rt(std::exp(t1)), f2 = sg * Rt(std::exp(t2));
+    for (int it = 0; it < 80; ++it) {
+      if (f1 > f2) {
+        tb = t2; t2 = t1; f2 = f1; t1 = tb - gr * (tb - ta); f1 = sg * Rt(std::exp(t1));
+      } else {
+        ta = t1; t1 = t2; f1 = f2; t2 = ta + gr * (tb - ta); f2 = sg * Rt(std::exp(t2));
+      }
+    }
+    const double best = std::max({sg * v[k], f1, f2}) * sg;
+    lo = std::min(lo, best);
+    hi = std::max(hi, best);
+  }
+  const double d0 = 2.0 / (lo + hi);
+  if (delta) *delta = (hi - lo) / (hi + lo);
+  std::vector<double> bl(n), s(n);
+  for (int l = 1; l <= n; ++l) {
+    const double co = cl[2 * l - 1];
+    double num = d0, den = 1.0;
+    for (int i = 1; i < n; ++i) num *= (cl[2 * i] - co);
+    for (int i = 1; i <= n; ++i)
+      if (i != l) den *= (cl[2 * i - 1] - co);
+    bl[l - 1] = num / den;
+    s[l - 1] = lmin * std::sqrt(co);
+  }
+  z.clear();
+  c.clear();
+  for (int l = 0; l < n; ++l) {
+    z.push_back(make_double2(0.0, s[l]));
+    c.push_back(make_double2(-0.5 * lmin * bl[l], 0.0));
+  }
+  for (int l = n - 1; l >= 0; --l) {
+    z.push_back(make_double2(0.0, -s[l]));
+    c.push_back(make_double2(-0.5 * lmin * bl[l], 0.0));
+  }
+  c0 = make_double2(0.0, 0.0);
+  return OV_OK;
+}
+
 namespace {
 
 // Number of eigenvalues of the symmetric tridiagonal (a, b) smaller than x (Sturm count).

@@ -234,6 +234,8 @@ int launch_force(ov_ctx* ctx, const double2* X, int nq, const double2* cq, doubl
 // host-side contour math (contour.cpp)
 void ellipse_rule(int n_q, double gamma, double rho, double alpha, int form, std::vector<double2>& z,
                   std::vector<double2>& c, double2& c0);
+int zolotarev_rule(int n, double lmin, double lmax, std::vector<double2>& z, std::vector<double2>& c, double2& c0,
+                   double* delta);
 double rational_value(double lam, const std::vector<double2>& z, const std::vector<double2>& c,
                       double2 c0);
 void tridiag_extreme_eigs(const std::vector<double>& a, const std::vector<double>& b, double* lo,

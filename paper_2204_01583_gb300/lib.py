@@ -37,7 +37,7 @@ EXPORTS = (
     "ov_set_contour_ellipse", "ov_get_contour", "ov_place_contour", "ov_sgn_HW_apply", "ov_overlap_apply",
     "ov_sgn_vjp", "ov_overlap_vjp", "ov_set_kernel_timing", "ov_kernel_times", "ov_version",
     "ov_apply_HW_noalloc", "ov_set_hw32_variant", "ov_hw32_variants", "ov_set_persistent", "ov_overlap_solve",
-    "ov_set_concurrency",
+    "ov_set_concurrency", "ov_zolotarev_rule", "ov_set_contour_zolotarev", "ov_place_zolotarev",
 )
 
 
@@ -92,6 +92,9 @@ def _load():
         "ov_set_hw32_variant": [vp, i],
         "ov_set_persistent": [vp, i],
         "ov_set_concurrency": [vp, i],
+        "ov_zolotarev_rule": [i, d, d, dp, dp, dp],
+        "ov_set_contour_zolotarev": [vp, i, d, d, dp],
+        "ov_place_zolotarev": [vp, i, i, ctypes.POINTER(Spectrum), vp],
         "ov_hw32_variants": [i, ip, ip, ip],
         "ov_overlap_solve": [vp, d, vp, vp, i, ctypes.POINTER(SolveOpts), d, i, ctypes.POINTER(Stats), vp],
     }
@@ -270,6 +273,18 @@ class Context:
         self._check(_lib.ov_set_hw32_variant(self._h, int(k)))
 
     # ------------------------------------------------------------------ timing
+    def set_contour_zolotarev(self, n_poles, lambda_min, lambda_max):
+        """Zolotarev node set on [lambda_min, lambda_max]; returns its maximum error delta."""
+        dl = ctypes.c_double(0.0)
+        self._check(_lib.ov_set_contour_zolotarev(self._h, int(n_poles), float(lambda_min), float(lambda_max),
+                                                  ctypes.byref(dl)))
+        return dl.value
+
+    def place_zolotarev(self, n_poles, steps=100, stream=None):
+        sp = Spectrum()
+        self._check(_lib.ov_place_zolotarev(self._h, int(n_poles), int(steps), ctypes.byref(sp), _stream_ptr(stream)))
+        return sp.as_dict()
+
     def set_concurrency(self, groups=0):
         """Parallel graph branches over groups of sources (0 = automatic)."""
         self._check(_lib.ov_set_concurrency(self._h, int(groups)))
@@ -302,6 +317,21 @@ def hw32_variants():
         _lib.ov_hw32_variants(k, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
         out.append((a.value, b.value, c.value))
     return out
+
+
+def zolotarev_rule(n_poles, lambda_min, lambda_max):
+    """(z, c, c0, delta) of the library's Zolotarev node set (host computation, no GPU)."""
+    import numpy as np
+
+    z = np.zeros(2 * int(n_poles), dtype=np.complex128)
+    c = np.zeros_like(z)
+    dl = ctypes.c_double(0.0)
+    rc = _lib.ov_zolotarev_rule(int(n_poles), float(lambda_min), float(lambda_max),
+                                z.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(dl))
+    if rc != 0:
+        raise OvError(rc, "ov_zolotarev_rule: bad arguments")
+    return z, c, 0.0 + 0.0j, dl.value
 
 
 def version():

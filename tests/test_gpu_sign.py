@@ -242,3 +242,41 @@ def test_source_groups_give_identical_results(gpu_lib, config2, mode):
     ctx.set_concurrency(0)
     for o, st in outs[1:]:
         assert np.array_equal(o, outs[0][0]) and st["iterations"] == outs[0][1]["iterations"]
+
+
+def test_zolotarev_nodes_4x4(gpu_lib):
+    """Zolotarev node set (16 pole pairs) placed from Lanczos bounds on 4^4: parity with the
+    per-node oracle on the same nodes, and the exact sign function (dense zheevd) within
+    the predicted error, far below the 32-node ellipse's."""
+    dims = (4, 4, 4, 4)
+    ctx, U = make_ctx(gpu_lib, dims, 0.3, S.seed_for("config1"))
+    spec = ctx.place_zolotarev(16, steps=120)
+    b = S.gaussian_spinor(dims, S.seed_for("config1.b"))
+    got, st = sgn_gpu(ctx, b, tol=1e-13, mode="fp64_2pass")
+    assert rel(got, _oracle(U, b, ctx)) < PARITY
+    lam, V = np.linalg.eigh(wilson.dense_HW(U, M0))
+    assert spec["gap"] <= np.abs(lam).min() and spec["abs_max_bound"] >= np.abs(lam).max()
+    assert spec["predicted_error"] < 1e-12
+    exact = (V * np.sign(lam)) @ (V.conj().T @ b.reshape(-1))
+    assert np.linalg.norm(got.reshape(-1) - exact) / np.linalg.norm(b) <= 1e-11
+
+
+@pytest.mark.parametrize("mode", ["fp64_2pass", "f32x2"])
+def test_zolotarev_nodes_8x4_sign_squared(gpu_lib, config2, mode):
+    """8^4 config-2 links with 16 Zolotarev pole pairs: sgn^2 b = b to 1e-10 (the 64-node
+    ellipse reaches only its ~1e-8 method error); the ellipse is restored afterwards."""
+    import torch
+
+    ctx, U, b, spec, want0 = config2
+    z, c, c0 = ctx.get_contour()
+    try:
+        zs = ctx.place_zolotarev(16, steps=150)
+        assert zs["predicted_error"] < 1e-11
+        got, st = sgn_gpu(ctx, b, nrhs=4, tol=1e-13, mode=mode)
+        S2 = torch.empty_like(to_dev(got))
+        ctx.sgn(to_dev(got), S2, 4, ctx.opts(mode=mode, tol=1e-13))
+        s2 = to_host(S2)
+        for k in range(4):
+            assert rel(s2[k], b[k]) < 1e-10
+    finally:
+        ctx.set_contour(z, c, c0)
