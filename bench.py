@@ -552,7 +552,7 @@ def run_dslash(args, wl):
         n, ms = ctx.kernel_times()["hw_kernel"]
         ctx.set_kernel_timing(False)
         # plain, 12-real, broadcast (re,re,im,im), padded float4 pairs (5 per link), 12-real float4
-        link_reals = {0: 72, 1: 48, 2: 144, 3: 80, 4: 48}[comp]
+        link_reals = {0: 72, 1: 48, 2: 144, 3: 80, 4: 48, 5: 48}[comp]
         by = V * (link_reals * s_real + nrhs * 48 * s_real)  # links once per launch; each RHS in + out
         per = ms / n / 1e3
         rows.append({"variant": k, "rhs_tile": rt, "compressed_links": bool(comp), "threads": nt,

@@ -245,7 +245,10 @@ int ov_overlap_solve(ov_ctx* ctx, double m_q, const void* b, void* x, int nrhs, 
  * layout with paired FP32 instructions and broadcast links; 3 and 4 spin-paired float4
  * layout (one 16-byte load per spin pair) with plain (padded) or 12-real links.
  * rhs_tile 0: four threads per site (one per direction), partial sums combined in
- * shared memory. */
+ * shared memory.  compressed 5: spin-paired layout with one xy-plane per block
+ * (threads reported as 0: Lx Ly of them; needs Lx Ly a multiple of 32, <= 1024), the
+ * plane's 12-real links staged in shared memory for rhs_tile right-hand sides and the
+ * plane's spinor staged per right-hand side. */
 int ov_set_hw32_variant(ov_ctx* ctx, int k);
 int ov_hw32_variants(int k, int* rhs_tile, int* compressed, int* threads);
 

@@ -297,7 +297,9 @@ int ov_apply_HW(ov_ctx* ctx, const void* in, void* out, int nrhs, int precision,
     if ((st = launch_unpack64(ctx, b, (double2*)out, nrhs, s))) return st;
   } else {
     const int npair = (nrhs + 1) / 2;
-    const int kpair = hw32_variant_count();  // then kpair + 1, kpair + 2: spin-paired float4 layout
+    // then kpair + 1, kpair + 2: spin-paired float4 layout; kpair + 3: the same with one
+    // xy-plane per block and links staged in shared memory (lattices with Lx Ly = 32k <= 1024)
+    const int kpair = hw32_variant_count();
     float2* a = (float2*)ws_get(ctx, "hw.a32", sizeof(float2) * n, &st);
     float2* b = (float2*)ws_get(ctx, "hw.b32", sizeof(float2) * n, &st);
     float4* pa = (float4*)ws_get(ctx, "hw.pa32", sizeof(float4) * 12 * (size_t)ctx->g.V * npair, &st);
@@ -322,13 +324,18 @@ int ov_apply_HW(ov_ctx* ctx, const void* in, void* out, int nrhs, int precision,
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        for (int kk = kpair; kk <= kpair + 2; ++kk) {
+        for (int kk = kpair; kk <= kpair + 3; ++kk) {
           if (kk == kpair) {
             if ((st = launch_pack_pair32(ctx, (const float2*)in, pa, nrhs, s))) return st;
             if ((st = launch_hw_pair(ctx, pa, pb, npair, s))) return st;  // warm (builds the links)
           } else {
             if ((st = launch_pack_s4(ctx, (const float2*)in, sa, nrhs, s))) return st;
-            if ((st = launch_hw32_s4(ctx, sa, sb, nrhs, kk - kpair - 1, s))) return st;
+            st = launch_hw32_s4(ctx, sa, sb, nrhs, kk - kpair - 1, s);
+            if (st == OV_ERR_INVALID_ARG) {  // this lattice does not fit the variant
+              st = OV_OK;
+              continue;
+            }
+            if (st != OV_OK) return st;
           }
           cudaEventRecord(e0, s);
           for (int rep = 0; rep < 3; ++rep) {
@@ -734,7 +741,7 @@ int ov_overlap_vjp(ov_ctx* ctx, double m_q, const void* eta, const void* b, void
 
 int ov_set_hw32_variant(ov_ctx* ctx, int k) {
   if (!ctx) return OV_ERR_INVALID_ARG;
-  if (k < -1 || k > hw32_variant_count() + 2) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "no such FP32 stencil variant");
+  if (k < -1 || k > hw32_variant_count() + 3) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "no such FP32 stencil variant");
   ctx->hw32_force = k;
   return OV_OK;
 }
@@ -742,14 +749,16 @@ int ov_set_hw32_variant(ov_ctx* ctx, int k) {
 int ov_hw32_variants(int k, int* rhs_tile, int* compressed, int* threads) {
   const int n = hw32_variant_count();
   if (k >= 0 && k < n && rhs_tile && compressed && threads) hw32_variant_info(k, rhs_tile, compressed, threads);
-  if (k >= n && k <= n + 2 && rhs_tile && compressed && threads) {
+  if (k >= n && k <= n + 3 && rhs_tile && compressed && threads) {
     // n: right-hand-side-paired layout, paired FP32 instructions, broadcast links;
-    // n + 1, n + 2: spin-paired float4 layout with plain (padded) or 12-real links
-    *rhs_tile = (k == n) ? 2 : 1;
+    // n + 1, n + 2: spin-paired float4 layout with plain (padded) or 12-real links;
+    // n + 3: spin-paired layout, one xy-plane per block (Lx Ly threads), 12-real links and
+    // the plane's spinor staged in shared memory, 4 right-hand sides per block
+    *rhs_tile = (k == n) ? 2 : (k == n + 3 ? 4 : 1);
     *compressed = 2 + (k - n);
-    *threads = 128;
+    *threads = (k == n + 3) ? 0 : 128;
   }
-  return n + 3;
+  return n + 4;
 }
 
 int ov_set_concurrency(ov_ctx* ctx, int groups) {

@@ -82,14 +82,15 @@ def test_hw_rejects_bad_arguments(gpu_lib):
     assert e.value.code == gpu_lib.OV_ERR_NO_GAUGE
 
 
-@pytest.mark.parametrize("variant", list(range(12)))
+@pytest.mark.parametrize("variant", list(range(13)))
 def test_hw_fp32_variants(gpu_lib, variant):
     """Every FP32 stencil variant (RHS tile, link compression, block size) against the
     oracle, with a right-hand-side count that leaves a ragged last tile."""
     import torch
 
-    assert len(gpu_lib.hw32_variants()) == 12
-    dims = (6, 4, 5, 4)
+    assert len(gpu_lib.hw32_variants()) == 13
+    plane = gpu_lib.hw32_variants()[variant][1] == 5  # one xy-plane per block: Lx Ly = 32k
+    dims = (8, 4, 5, 3) if plane else (6, 4, 5, 4)
     ctx, U = make_ctx(gpu_lib, dims, 0.6, 71)
     ctx.set_hw32_variant(variant)
     nrhs = 7
@@ -114,3 +115,23 @@ def test_hw_fp32_autotuned_12rhs_16x32(gpu_lib):
     got = to_host(out).astype(np.complex128)
     for k in (0, 11):
         assert rel(got[k], cimpl.hw_apply(U, psi[k].astype(np.complex128), M0)) < 3e-6
+
+
+def test_hw_fp32_plane_variant_rejects_unfit_lattice(gpu_lib):
+    """The plane-staged variant needs Lx Ly to be a multiple of 32: forced on another
+    lattice it reports OV_ERR_INVALID_ARG, and the autotuner skips it there."""
+    import torch
+
+    dims = (6, 4, 5, 4)
+    ctx, U = make_ctx(gpu_lib, dims, 0.6, 73)
+    psi = to_dev(S.gaussian_spinor(dims, 74, n=2).astype(np.complex64))
+    out = torch.empty_like(psi)
+    k = [i for i, v in enumerate(gpu_lib.hw32_variants()) if v[1] == 5][0]
+    ctx.set_hw32_variant(k)
+    with pytest.raises(gpu_lib.OvError) as e:
+        ctx.apply_HW(psi, out, 2, gpu_lib.OV_FP32)
+    assert e.value.code == gpu_lib.OV_ERR_INVALID_ARG
+    ctx.set_hw32_variant(-1)
+    ctx.apply_HW(psi, out, 2, gpu_lib.OV_FP32)
+    want = wilson.apply_HW(U, to_host(psi).astype(np.complex128), M0)
+    assert rel(to_host(out).astype(np.complex128), want) < 1e-5
