@@ -753,8 +753,8 @@ int ov_hw32_variants(int k, int* rhs_tile, int* compressed, int* threads) {
     // n: right-hand-side-paired layout, paired FP32 instructions, broadcast links;
     // n + 1, n + 2: spin-paired float4 layout with plain (padded) or 12-real links;
     // n + 3: spin-paired layout, one xy-plane per block (Lx Ly threads), 12-real links and
-    // the plane's spinor staged in shared memory, 4 right-hand sides per block
-    *rhs_tile = (k == n) ? 2 : (k == n + 3 ? 4 : 1);
+    // the plane's spinor staged in shared memory, 6 right-hand sides per block
+    *rhs_tile = (k == n) ? 2 : (k == n + 3 ? 6 : 1);
     *compressed = 2 + (k - n);
     *threads = (k == n + 3) ? 0 : 128;
   }
