@@ -262,7 +262,7 @@ int ov_set_persistent(ov_ctx* ctx, int enable);
 /* Sources of one call are independent; the per-iteration kernels replayed from a CUDA
  * graph can run as `groups` parallel branches, each over a contiguous block of sources,
  * which fills the launch tails and serial reduction steps of small lattices.  groups = 0
- * (default): two branches when there are >= 2 sources and the stencil grid of all sources
+ * (default): one branch per source, at most four, when the stencil grid of all sources
  * fits two waves of the GPU, else one; groups >= 1: that many (capped at the source
  * count).  Results do not depend on it (every source's arithmetic is the same).
  * Errors: OV_ERR_INVALID_ARG for groups outside [0, 64]. */
