@@ -40,6 +40,31 @@ void* ws_get(ov_ctx* ctx, const char* name, size_t bytes, int* status) {
   cudaError_t e = cudaMalloc(&b.p, nb);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    // Out of memory: release the stored Krylov bases ("<tag>.ring" of the stored-basis
+    // forms, the largest workspaces, rebuilt on demand) of every solver form other than the
+    // requesting one -- those are idle -- and retry once.
+    const std::string nm(name), tag = nm.substr(0, nm.find('.'));
+    bool freed = false;
+    for (auto& kv : ctx->bufs) {
+      const std::string& k = kv.first;
+      const bool ring = k.size() > 6 && k.compare(k.size() - 6, 6, "s.ring") == 0;
+      if (kv.second.p && ring && k.substr(0, k.find('.')) != tag) {
+        cudaDeviceSynchronize();
+        cudaFree(kv.second.p);
+        kv.second.p = nullptr;
+        kv.second.bytes = 0;
+        freed = true;
+      }
+    }
+    if (freed) {
+      graphs_release(ctx);
+      e = cudaMalloc(&b.p, nb);
+      if (e == cudaSuccess) {
+        b.bytes = nb;
+        return b.p;
+      }
+      cudaGetLastError();
+    }
     b.p = nullptr;
     *status = ctx_fail(ctx, OV_ERR_OUT_OF_MEMORY,
                        std::string("cudaMalloc of workspace '") + name + "' (" + std::to_string(nb) + " bytes) failed");
@@ -270,6 +295,7 @@ int ov_set_gauge(ov_ctx* ctx, const double* U, int on_device, void* stream) {
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "ov_set_gauge");
   kt_collect(ctx);
   ctx->have_gauge = true;
+  ctx->coef_iter_hint = 0;
   ctx->have_c32 = false;
   ctx->have_b32 = false;
   ctx->have_s4 = false;
@@ -390,6 +416,7 @@ int ov_set_contour(ov_ctx* ctx, int n, const double* z, const double* c, double 
   ctx->c = cc;
   ctx->c0 = make_double2(c0_re, c0_im);
   ctx->have_contour = true;
+  ctx->coef_iter_hint = 0;
   return OV_OK;
 }
 
@@ -407,6 +434,7 @@ int ov_set_contour_ellipse(ov_ctx* ctx, int n_q, double gamma, double rho, doubl
   ctx->c = c;
   ctx->c0 = c0;
   ctx->have_contour = true;
+  ctx->coef_iter_hint = 0;
   return OV_OK;
 }
 
@@ -529,6 +557,7 @@ int ov_set_contour_zolotarev(ov_ctx* ctx, int n_poles, double lambda_min, double
   ctx->c = c;
   ctx->c0 = c0;
   ctx->have_contour = true;
+  ctx->coef_iter_hint = 0;
   return OV_OK;
 }
 

@@ -56,16 +56,22 @@ extern const char* const kKernelClassNames[KC_COUNT];
 
 // Graph cache entry for the per-iteration kernels of a solve: every pointer the
 // captured launches read, plus the launch shape.
+// Identity of a captured graph: the workspace pointers and every size that enters the
+// captured kernel arguments (per-source offsets of grouped branches depend on the slot
+// count and the history length).
 struct GraphKey {
   const void* ptr[4];
   int nsrc, nshift, flavour, chunk;
+  int nslots = 0, hist_len = 0;
   bool operator<(const GraphKey& o) const {
     for (int k = 0; k < 4; ++k)
       if (ptr[k] != o.ptr[k]) return ptr[k] < o.ptr[k];
     if (nsrc != o.nsrc) return nsrc < o.nsrc;
     if (nshift != o.nshift) return nshift < o.nshift;
     if (flavour != o.flavour) return flavour < o.flavour;
-    return chunk < o.chunk;
+    if (chunk != o.chunk) return chunk < o.chunk;
+    if (nslots != o.nslots) return nslots < o.nslots;
+    return hist_len < o.hist_len;
   }
 };
 
@@ -87,6 +93,8 @@ struct ov_ctx {
   int hw32_force = -1;                 // ov_set_hw32_variant
   bool no_coop = true;                 // ov_set_persistent(ctx, 1) enables the persistent loop
   int groups = 0;                      // ov_set_concurrency: source groups per graph (0 = auto)
+  int coef_iter_hint = 0;              // Krylov iterations of the last converged coefficient-space
+                                       // solve (sizes the stored basis); reset with gauge or contour
 
   // quadrature S_N = c0 + sum_j c_j (z_j - H)^-1
   std::vector<double2> z, c;

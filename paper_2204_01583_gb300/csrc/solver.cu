@@ -1122,7 +1122,7 @@ int run_iterations(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, int nshift, int f
   if (graph) {
     const int G = source_groups(ctx, nsrc, w.nblk1);
     GraphKey key{{(const void*)w.a.ring, (const void*)w.a.p, (const void*)w.a.x, (const void*)w.a.sacc},
-                 nsrc, nshift, flavour * 128 + G, chunk};
+                 nsrc, nshift, flavour * 128 + G, chunk, w.nslots, w.max_iter};
     auto it = ctx->graphs.find(key);
     if (it != ctx->graphs.end()) {
       exec = it->second;
@@ -1426,20 +1426,79 @@ static int solve_sign_stored(ov_ctx* ctx, const double2* b_soa, double2* out_soa
 // s = c0 b + sum_i g_i v_i.  Same result as OV_MODE_FP64 up to rounding; the vector
 // work no longer grows with the number of nodes.
 template <typename R>
+static int solve_sign_regen(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc,
+                            const ov_solve_opts& o, SolveOut* so, cudaStream_t s);
+
+// Fold the statistics of one batch of sources into the call's.
+void merge_stats(SolveOut* tot, const SolveOut& b, bool first) {
+  if (first) {
+    *tot = b;
+    return;
+  }
+  tot->iterations = std::max(tot->iterations, b.iterations);
+  tot->converged = tot->converged && b.converged;
+  tot->max_residual = std::max(tot->max_residual, b.max_residual);
+  tot->error_bound = std::max(tot->error_bound, b.error_bound);
+  tot->refine_rounds += b.refine_rounds;
+  tot->inner_iterations += b.inner_iterations;
+  tot->node_updates += b.node_updates;
+  tot->launches += b.launches;
+}
+
+// Coefficient-space solve.  Preferred: keep the Lanczos basis in HBM (pass 2 is one read
+// of it instead of a second Lanczos pass), for as many sources at a time as fit the store
+// budget -- 40% of device memory, and no more than what is free beyond a 10% reserve (a
+// store this context already holds counts as free).  The store depth is min(max_iter,
+// 1024) vectors, or 1.25x the iterations of the previous batch or call (plus 32) once
+// those are known; a batch that outgrows its store, or that cannot be allocated, is
+// solved by regenerating the basis instead.  OV_MODE_FP64_REGEN always regenerates.
+template <typename R>
 static int solve_sign_coef(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc, const ov_solve_opts& o,
                            SolveOut* so, cudaStream_t s) {
-  const int ns = (int)ctx->z.size();
-  // Keep the whole basis in HBM when up to min(max_iter, 1024) vectors per source fit a
-  // quarter of the device: then pass 2 is one read of the basis instead of a second
-  // Lanczos pass.  Otherwise (or if the solve outgrows the store) regenerate.
+  if (o.mode == OV_MODE_FP64_REGEN) return solve_sign_regen<R>(ctx, b_soa, out_soa, nsrc, o, so, s);
   size_t freeb = 0, totalb = 0;
   cudaMemGetInfo(&freeb, &totalb);
-  const int cap = std::min(o.max_iter, 1024);
-  const double store_bytes = (double)(cap + 2) * nsrc * 12.0 * ctx->g.V * sizeof(double2);
-  if (o.mode != OV_MODE_FP64_REGEN && store_bytes <= 0.25 * (double)totalb) {
-    const int st = solve_sign_stored<R>(ctx, b_soa, out_soa, nsrc, o, so, s, cap);
-    if (st != OV_ERR_NOT_CONVERGED || cap >= o.max_iter) return st;
+  const std::string ring = std::string(coef_tag<R>()) + "s.ring";
+  auto it = ctx->bufs.find(ring);
+  const double held = it != ctx->bufs.end() ? (double)it->second.bytes : 0.0;
+  const double budget = std::min(0.40 * (double)totalb, (double)freeb + held - 0.10 * (double)totalb);
+  const size_t n12 = (size_t)12 * ctx->g.V;
+  const double per_vec = (double)n12 * sizeof(double2);
+  int cap = std::min(o.max_iter, ctx->coef_iter_hint > 0 ? std::max(64, ctx->coef_iter_hint * 5 / 4 + 32) : 1024);
+  int r0 = 0, worst = OV_OK;
+  bool first = true;
+  while (r0 < nsrc) {
+    const int rem = nsrc - r0;
+    const int nb_max = (int)std::min<double>(rem, std::floor(budget / ((cap + 3) * per_vec)));
+    const int nbat = nb_max >= 1 ? (rem + nb_max - 1) / nb_max : 1;
+    const int nb = nb_max >= 1 ? (rem + nbat - 1) / nbat : rem;  // even batches
+    SolveOut sb;
+    int st = OV_ERR_OUT_OF_MEMORY;
+    if (nb_max >= 1) st = solve_sign_stored<R>(ctx, b_soa + r0 * n12, out_soa + r0 * n12, nb, o, &sb, s, cap);
+    if (st == OV_ERR_OUT_OF_MEMORY || (st == OV_ERR_NOT_CONVERGED && cap < o.max_iter)) {
+      cudaGetLastError();
+      sb = SolveOut();
+      st = solve_sign_regen<R>(ctx, b_soa + r0 * n12, out_soa + r0 * n12, nb, o, &sb, s);
+    }
+    if (st != OV_OK && st != OV_ERR_NOT_CONVERGED) return st;
+    if (st == OV_ERR_NOT_CONVERGED) worst = st;
+    merge_stats(so, sb, first);
+    first = false;
+    if (sb.converged) {
+      ctx->coef_iter_hint = sb.iterations;
+      cap = std::min(o.max_iter, std::max(64, sb.iterations * 5 / 4 + 32));
+    }
+    r0 += nb;
   }
+  return worst;
+}
+
+// OV_MODE_FP64_REGEN and the fallback of the stored form: pass 1 records alpha_i, beta_i,
+// pass 2 regenerates v_1 .. v_k with bit-identical arithmetic and sums g_i v_i.
+template <typename R>
+static int solve_sign_regen(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc,
+                            const ov_solve_opts& o, SolveOut* so, cudaStream_t s) {
+  const int ns = (int)ctx->z.size();
   SolveWs<R> w;
   const std::string tag = coef_tag<R>();
   int st = setup_ws<R>(ctx, nsrc, ns, false, true, true, o.max_iter, &w, tag.c_str());
@@ -1516,7 +1575,7 @@ static int solve_sign_coef(ov_ctx* ctx, const double2* b_soa, double2* out_soa, 
   if (graph && kmax >= chunk) {
     const int G = source_groups(ctx, nsrc, w.nblk1);
     GraphKey key{{(const void*)w.a.ring, (const void*)gco, (const void*)w.a.sacc, (const void*)w.a.hist_a},
-                 nsrc, ns, 3 * 128 + G, chunk};
+                 nsrc, ns, 3 * 128 + G, chunk, w.nslots, w.max_iter};
     auto it = ctx->graphs.find(key);
     if (it != ctx->graphs.end()) {
       exec = it->second;

@@ -280,3 +280,22 @@ def test_zolotarev_nodes_8x4_sign_squared(gpu_lib, config2, mode):
             assert rel(s2[k], b[k]) < 1e-10
     finally:
         ctx.set_contour(z, c, c0)
+
+
+@pytest.mark.parametrize("mode", ["fp64_2pass", "f32x2"])
+def test_store_depth_changes_reuse_no_stale_graph(gpu_lib, config2, mode):
+    """Calls with different stored-basis depths (max_iter, and the depth learned from the
+    previous call) on one context give the results of a fresh context: graphs captured for
+    one depth are not replayed for another."""
+    ctx, U, b, spec, want0 = config2
+    a1, _ = sgn_gpu(ctx, b, nrhs=4, tol=1e-12, mode=mode, max_iter=2000)
+    a2, _ = sgn_gpu(ctx, b, nrhs=4, tol=1e-12, mode=mode, max_iter=600)
+    a3, _ = sgn_gpu(ctx, b, nrhs=4, tol=1e-12, mode=mode)
+    fresh, _ = make_ctx(gpu_lib, (8, 8, 8, 8), 0.5, S.seed_for("config2"))
+    z, c, c0 = ctx.get_contour()
+    fresh.set_contour(z, c, c0)
+    want, _ = sgn_gpu(fresh, b, nrhs=4, tol=1e-12, mode=mode, max_iter=2000)
+    for got in (a1, a2, a3):
+        assert np.all(np.isfinite(got))
+        for k in range(4):
+            assert rel(got[k], want[k]) < 1e-13
