@@ -63,6 +63,8 @@ WORKLOADS = {
     # overlap solve x = D_ov^-1 b (CG on the normal equations, double-float inner solves)
     "ovsolve-8^4-mq0.05-4src": dict(dims=(8, 8, 8, 8), eps=0.5, m_q=0.05, n_q=64, nsrc=4, src="gauss", tol=1e-10,
                                     inner_tol=1e-12, mode="f32x2", kind="ovsolve"),
+    # gradient of Re<eta, sgn(H_W) b> w.r.t. b and the links (adjoint solves + fused force)
+    "vjp-8^4-nq48": dict(dims=(8, 8, 8, 8), eps=0.4, n_q=48, nsrc=1, src="gauss", tol=1e-12, kind="vjp"),
     # the same measure with Zolotarev's optimal node set (n pole pairs = 2n nodes) from Lanczos bounds
     "sigma-8^4-zolotarev": dict(dims=(8, 8, 8, 8), eps=0.5, nsrc=4, src="gauss", kind="sigma", rule="zolotarev",
                                 n_list=(4, 8, 12, 16, 20)),
@@ -642,6 +644,61 @@ def run_sigma(args, wl):
     return 0
 
 
+def run_vjp(args, wl):
+    """Gradients per second: ov_sgn_vjp (grad_b = S_N^dag eta and the su(3) link force of
+    L = Re<eta, S_N b>) for one source, L2 flushed between timed evaluations."""
+    import torch
+
+    from paper_2204_01583_gb300 import build as build_lib
+
+    build_lib()
+    from paper_2204_01583_gb300 import lib
+    import synthetic as S
+
+    dims = wl["dims"]
+    U = S.su3_links(dims, wl["eps"], S.seed_for("config4"))
+    ctx = lib.Context(dims, bc_t=-1, m0=M0)
+    ctx.set_gauge(torch.from_numpy(U).cuda())
+    spec = ctx.place_contour(wl["n_q"], steps=150)
+    b = torch.from_numpy(S.gaussian_spinor(dims, S.seed_for("config4.b"))).cuda()
+    eta = torch.from_numpy(S.gaussian_spinor(dims, S.seed_for("config4.eta"))).cuda()
+    gb = torch.empty_like(b)
+    F = torch.empty((4,) + tuple(b.shape[:4]) + (8,), dtype=torch.float64, device="cuda")
+    o = ctx.opts(tol=wl["tol"])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        ctx.sgn_vjp(eta, b, gb, F, o)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    ts, st = [], None
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = ctx.sgn_vjp(eta, b, gb, F, o)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    ctx.set_kernel_timing(True)
+    ctx.sgn_vjp(eta, b, gb, F, o)
+    torch.cuda.synchronize()
+    kt = {k: {"launches": n, "ms": ms} for k, (n, ms) in ctx.kernel_times().items() if n}
+    ctx.set_kernel_timing(False)
+    ms = sum(ts) / len(ts)
+    line = {"metric": "gradients/s of Re<eta, sgn(H_W) b> (b and link force)", "value": 1e3 / ms,
+            "unit": "gradients/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "lattice": "x".join(map(str, dims)), "link_eps": wl["eps"],
+                       "N_q": wl["n_q"], "tol": wl["tol"], "l2": "256 MiB buffer written between timed steps"},
+            "clocks": clocks, "kernels_one_step": kt,
+            "solver": {"iterations": st["iterations"], "converged": st["converged"], "spectrum": spec}}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ovsolve(args, wl):
     """Overlap solves per second: x = D_ov(m_q)^-1 b for all sources in one call, L2 flushed
     between timed solves; the line carries the CG iteration count, the D applies and the
@@ -700,6 +757,8 @@ def main():
     wl = WORKLOADS[args.workload]
     if wl.get("kind") == "dslash":
         return run_dslash(args, wl)
+    if wl.get("kind") == "vjp":
+        return run_vjp(args, wl)
     if wl.get("kind") == "ovsolve":
         return run_ovsolve(args, wl)
     if wl.get("kind") == "sigma":
