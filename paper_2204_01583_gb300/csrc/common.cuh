@@ -69,37 +69,6 @@ struct Cx {
   R re, im;
 };
 
-// A sum of double-float products with one normalisation at the end: the leading products
-// hi(x) hi(y) are summed by error-free two-sum into s, and every low-order term (the
-// exact error of each leading product, the cross terms hi lo + lo hi, the two-sum errors)
-// into c.  12 FP32 instructions per product against 15 for a normalised double-float FMA.
-struct DFSum {
-  float s, c;
-};
-// first product (s = 0: no two-sum needed)
-__device__ __forceinline__ DFSum dfs_first(float xh, float xl, float yh, float yl) {
-  const float p = __fmul_rn(xh, yh);
-  float c = __fmaf_rn(xh, yh, -p);
-  c = __fmaf_rn(xh, yl, c);
-  c = __fmaf_rn(xl, yh, c);
-  return {p, c};
-}
-__device__ __forceinline__ void dfs_add(DFSum& A, float xh, float xl, float yh, float yl) {
-  const float p = __fmul_rn(xh, yh);
-  float c = __fadd_rn(A.c, __fmaf_rn(xh, yh, -p));
-  c = __fmaf_rn(xh, yl, c);
-  c = __fmaf_rn(xl, yh, c);
-  const float s = __fadd_rn(A.s, p);
-  const float bb = __fsub_rn(s, A.s);
-  A.c = __fadd_rn(c, __fadd_rn(__fsub_rn(A.s, __fsub_rn(s, bb)), __fsub_rn(p, bb)));
-  A.s = s;
-}
-__device__ __forceinline__ DF dfs_get(DFSum A) {
-  float s, e;
-  df_two_sum(A.s, A.c, s, e);
-  return DF(s, e);
-}
-
 // Storage type of one complex number and its (un)packing, per arithmetic type.
 template <typename R> struct Store;
 template <> struct Store<double> {
@@ -384,41 +353,104 @@ __device__ __forceinline__ Cx<R> uphase(Cx<R> a, int q) {
   return (q & 2) ? Cx<R>{-t.re, -t.im} : t;
 }
 
-// u0 = sum_j l_j h0_j, u1 = sum_j l_j h1_j for one link row l (complex, 3 terms): the
-// generic form uses complex FMAs; double-float uses one DFSum per real output.
+// The half-spinor operand of the link-row products of one hop, and the products
+// u0 = sum_j l_j h0_j, u1 = sum_j l_j h1_j for a link row l (complex, 3 terms).
+// Generic: complex FMAs.
 template <typename R>
-__device__ __forceinline__ void row_products(const Cx<R> l[3], const Cx<R> h0[3], const Cx<R> h1[3], Cx<R>& u0,
-                                             Cx<R>& u1) {
-  u0 = {R(0), R(0)};
-  u1 = {R(0), R(0)};
+struct RowOperand {
+  Cx<R> h0[3], h1[3];
+  __device__ __forceinline__ void set(const Cx<R> a[3], const Cx<R> b[3]) {
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    u0 = cfma(l[j], h0[j], u0);
-    u1 = cfma(l[j], h1[j], u1);
-  }
-}
-__device__ __forceinline__ void row_products(const Cx<DF> l[3], const Cx<DF> h0[3], const Cx<DF> h1[3],
-                                             Cx<DF>& u0, Cx<DF>& u1) {
-  const Cx<DF>* hh[2] = {h0, h1};
-  Cx<DF>* uu[2] = {&u0, &u1};
-#pragma unroll
-  for (int sp = 0; sp < 2; ++sp) {
-    const Cx<DF>* h = hh[sp];
-    // re = sum_j (l.re h.re - l.im h.im), im = sum_j (l.re h.im + l.im h.re)
-    DFSum re = dfs_first(l[0].re.hi, l[0].re.lo, h[0].re.hi, h[0].re.lo);
-    DFSum im = dfs_first(l[0].re.hi, l[0].re.lo, h[0].im.hi, h[0].im.lo);
-    dfs_add(re, -l[0].im.hi, -l[0].im.lo, h[0].im.hi, h[0].im.lo);
-    dfs_add(im, l[0].im.hi, l[0].im.lo, h[0].re.hi, h[0].re.lo);
-#pragma unroll
-    for (int j = 1; j < 3; ++j) {
-      dfs_add(re, l[j].re.hi, l[j].re.lo, h[j].re.hi, h[j].re.lo);
-      dfs_add(re, -l[j].im.hi, -l[j].im.lo, h[j].im.hi, h[j].im.lo);
-      dfs_add(im, l[j].re.hi, l[j].re.lo, h[j].im.hi, h[j].im.lo);
-      dfs_add(im, l[j].im.hi, l[j].im.lo, h[j].re.hi, h[j].re.lo);
+    for (int j = 0; j < 3; ++j) {
+      h0[j] = a[j];
+      h1[j] = b[j];
     }
-    *uu[sp] = {dfs_get(re), dfs_get(im)};
   }
+  __device__ __forceinline__ void products(const Cx<R> l[3], Cx<R>& u0, Cx<R>& u1) const {
+    u0 = {R(0), R(0)};
+    u1 = {R(0), R(0)};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      u0 = cfma(l[j], h0[j], u0);
+      u1 = cfma(l[j], h1[j], u1);
+    }
+  }
+};
+
+// Double-float: the two spins of a half spinor run lane-wise on FP32 pairs (lane 0:
+// h0, lane 1: h1) with Blackwell's paired FP32 instructions (FMUL2/FFMA2/FADD2), so the
+// six double-float products of each real output cost about half the instructions.  Each
+// sum is a DFSum2 (value s - cn): leading products summed by error-free two-sum, all
+// low-order terms negated in cn; link values enter as broadcast pairs.
+__device__ __forceinline__ float2 bcast2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+struct DFSum2 {
+  float2 s, cn;
+};
+// x y for x = (xh, xl) broadcast (given as XH, -XH, -XL) and y = (YH, YL) per lane
+__device__ __forceinline__ DFSum2 dfs2_first(float2 XH, float2 NXH, float2 NXL, float2 YH, float2 YL) {
+  const float2 p = __fmul2_rn(XH, YH);
+  float2 cn = __ffma2_rn(NXH, YH, p);  // p - xh yh, exact
+  cn = __ffma2_rn(NXH, YL, cn);        // - xh yl
+  cn = __ffma2_rn(NXL, YH, cn);        // - xl yh
+  return {p, cn};
 }
+__device__ __forceinline__ void dfs2_add(DFSum2& A, float2 XH, float2 NXH, float2 NXL, float2 YH, float2 YL) {
+  const float2 p = __fmul2_rn(XH, YH);
+  float2 cn = __fadd2_rn(A.cn, __ffma2_rn(NXH, YH, p));
+  cn = __ffma2_rn(NXH, YL, cn);
+  cn = __ffma2_rn(NXL, YH, cn);
+  const float2 s = __fadd2_rn(A.s, p);  // two-sum of s + p
+  const float2 bb = f2sub(s, A.s);
+  const float2 err = __fadd2_rn(f2sub(A.s, f2sub(s, bb)), f2sub(p, bb));
+  A.cn = f2sub(cn, err);
+  A.s = s;
+}
+// s - cn normalised per lane: two-sum of s and -cn
+__device__ __forceinline__ void dfs2_get(const DFSum2& A, float2& hi, float2& lo) {
+  const float2 s = f2sub(A.s, A.cn);
+  const float2 bb = f2sub(s, A.s);
+  lo = f2sub(f2sub(A.s, f2sub(s, bb)), __fadd2_rn(A.cn, bb));
+  hi = s;
+}
+
+template <>
+struct RowOperand<DF> {
+  float2 yh_re[3], yl_re[3], yh_im[3], yl_im[3];  // lane 0: h0, lane 1: h1
+  __device__ __forceinline__ void set(const Cx<DF> a[3], const Cx<DF> b[3]) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      yh_re[j] = make_float2(a[j].re.hi, b[j].re.hi);
+      yl_re[j] = make_float2(a[j].re.lo, b[j].re.lo);
+      yh_im[j] = make_float2(a[j].im.hi, b[j].im.hi);
+      yl_im[j] = make_float2(a[j].im.lo, b[j].im.lo);
+    }
+  }
+  // re = sum_j (l.re h.re - l.im h.im), im = sum_j (l.re h.im + l.im h.re), both spins at once
+  __device__ __forceinline__ void products(const Cx<DF> l[3], Cx<DF>& u0, Cx<DF>& u1) const {
+    DFSum2 re, im;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float2 xr = bcast2(l[j].re.hi), nxr = bcast2(-l[j].re.hi), nxrl = bcast2(-l[j].re.lo);
+      const float2 xi = bcast2(l[j].im.hi), nxi = bcast2(-l[j].im.hi), nxil = bcast2(-l[j].im.lo);
+      const float2 xil = bcast2(l[j].im.lo);
+      if (j == 0) {
+        re = dfs2_first(xr, nxr, nxrl, yh_re[j], yl_re[j]);
+        im = dfs2_first(xr, nxr, nxrl, yh_im[j], yl_im[j]);
+      } else {
+        dfs2_add(re, xr, nxr, nxrl, yh_re[j], yl_re[j]);
+        dfs2_add(im, xr, nxr, nxrl, yh_im[j], yl_im[j]);
+      }
+      dfs2_add(re, nxi, xi, xil, yh_im[j], yl_im[j]);  // x = -l.im
+      dfs2_add(im, xi, nxi, nxil, yh_re[j], yl_re[j]);
+    }
+    float2 rh, rl, ih, il;
+    dfs2_get(re, rh, rl);
+    dfs2_get(im, ih, il);
+    u0 = {DF(rh.x, rl.x), DF(ih.x, il.x)};
+    u1 = {DF(rh.y, rl.y), DF(ih.y, il.y)};
+  }
+};
 
 // Phase 1 with one instruction stream for all directions and both hops: mu and the hop
 // are runtime values, A_mu is applied as a permutation and unit phases, and the rows
@@ -464,6 +496,8 @@ __device__ __forceinline__ void hw_split_phase1_compact(const typename Store<R>:
       h0[col] = cadd(p0, uphase(pa, qa0 + qd));
       h1[col] = cadd(p1, uphase(pb, qa1 + qd));
     }
+    RowOperand<R> hop;
+    hop.set(h0, h1);
     const typename Store<R>::T* Ul = U + (size_t)mu * 9 * V + sl;
 #pragma unroll 1
     for (int i = 0; i < 3; ++i) {
@@ -476,7 +510,7 @@ __device__ __forceinline__ void hw_split_phase1_compact(const typename Store<R>:
         if (dir) l[j].im = -l[j].im;
       }
       Cx<R> u0, u1;
-      row_products(l, h0, h1, u0, u1);
+      hop.products(l, u0, u1);
       const Cx<R> c0 = uphase(u0, qs), c1 = uphase(u1, qs);
       const Cx<R> c2 = uphase(swap ? u1 : u0, qb0 + qd + qs), c3 = uphase(swap ? u0 : u1, qb1 + qd + qs);
       Cx<R>* a = acc + i * kSplitSites;
