@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("dims,bc_t,nrhs", [((4, 4, 4, 4), -1, 1), ((3, 5, 4, 6), -1, 2), ((6, 4, 2, 5), 1, 3),
-                                            ((8, 8, 8, 8), -1, 2)])
+                                            ((8, 8, 8, 8), -1, 2), ((1, 2, 3, 4), -1, 2), ((5, 1, 1, 3), 1, 1)])
 def test_hw_fp64_matches_oracle(gpu_lib, dims, bc_t, nrhs):
     import torch
 
@@ -27,7 +27,7 @@ def test_hw_fp64_matches_oracle(gpu_lib, dims, bc_t, nrhs):
         assert np.abs(got[0] - wilson.apply_HW(U, psi[0], M0, bc_t=float(bc_t))).max() < 1e-13
 
 
-@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (5, 3, 4, 6), (16, 16, 16, 16)])
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (5, 3, 4, 6), (16, 16, 16, 16), (1, 2, 3, 4)])
 def test_hw_fp32_matches_oracle(gpu_lib, dims):
     import torch
 

@@ -299,3 +299,30 @@ def test_store_depth_changes_reuse_no_stale_graph(gpu_lib, config2, mode):
         assert np.all(np.isfinite(got))
         for k in range(4):
             assert rel(got[k], want[k]) < 1e-13
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (1, 2, 3, 4), (5, 1, 1, 3)])
+@pytest.mark.parametrize("mode", ["fp64", "fp64_2pass", "f32x2"])
+def test_degenerate_lattices(gpu_lib, dims, mode):
+    """Extents 1 and 2, where a site is its own neighbour or both neighbours coincide:
+    parity with the oracle (which builds the hops with periodic rolls)."""
+    ctx, U = make_ctx(gpu_lib, dims, 0.5, 57)
+    ctx.set_contour_ellipse(24, 3.4, 3.4, 0.3)
+    b = S.gaussian_spinor(dims, 58, n=2)
+    got, st = sgn_gpu(ctx, b, tol=1e-12, mode=mode)
+    for k in range(2):
+        assert rel(got[k], _oracle(U, b[k], ctx)) < PARITY
+
+
+def test_many_sources_one_call(gpu_lib):
+    """40 sources in one call (more than any graph-branch or batch count): each equals
+    its solve alone."""
+    dims = (4, 4, 4, 4)
+    ctx, U = make_ctx(gpu_lib, dims, 0.3, 61)
+    ctx.set_contour_ellipse(16, 3.4, 3.4, 0.3)
+    b = S.gaussian_spinor(dims, 62, n=40)
+    for mode in ("fp64_2pass", "f32x2"):
+        allb, st = sgn_gpu(ctx, b, nrhs=40, tol=1e-12, mode=mode)
+        for k in (0, 17, 39):
+            one, _ = sgn_gpu(ctx, b[k], tol=1e-12, mode=mode)
+            assert rel(allb[k], one) < 1e-12
