@@ -64,7 +64,8 @@ WORKLOADS = {
     "ovsolve-8^4-mq0.05-4src": dict(dims=(8, 8, 8, 8), eps=0.5, m_q=0.05, n_q=64, nsrc=4, src="gauss", tol=1e-10,
                                     inner_tol=1e-12, mode="f32x2", kind="ovsolve"),
     # gradient of Re<eta, sgn(H_W) b> w.r.t. b and the links (adjoint solves + fused force)
-    "vjp-8^4-nq48": dict(dims=(8, 8, 8, 8), eps=0.4, n_q=48, nsrc=1, src="gauss", tol=1e-12, kind="vjp"),
+    "vjp-8^4-nq48": dict(dims=(8, 8, 8, 8), eps=0.4, n_q=48, nsrc=1, src="gauss", tol=1e-12, kind="vjp",
+                         mode="fp64"),
     # the same measure with Zolotarev's optimal node set (n pole pairs = 2n nodes) from Lanczos bounds
     "sigma-8^4-zolotarev": dict(dims=(8, 8, 8, 8), eps=0.5, nsrc=4, src="gauss", kind="sigma", rule="zolotarev",
                                 n_list=(4, 8, 12, 16, 20)),
@@ -664,7 +665,8 @@ def run_vjp(args, wl):
     eta = torch.from_numpy(S.gaussian_spinor(dims, S.seed_for("config4.eta"))).cuda()
     gb = torch.empty_like(b)
     F = torch.empty((4,) + tuple(b.shape[:4]) + (8,), dtype=torch.float64, device="cuda")
-    o = ctx.opts(tol=wl["tol"])
+    mode = args.mode or wl["mode"]
+    o = ctx.opts(mode=mode, tol=wl["tol"])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         ctx.sgn_vjp(eta, b, gb, F, o)
@@ -689,9 +691,11 @@ def run_vjp(args, wl):
     ms = sum(ts) / len(ts)
     line = {"metric": "gradients/s of Re<eta, sgn(H_W) b> (b and link force)", "value": 1e3 / ms,
             "unit": "gradients/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[mode],
+            "data": "synthetic",
             "config": {"workload": args.workload, "lattice": "x".join(map(str, dims)), "link_eps": wl["eps"],
-                       "N_q": wl["n_q"], "tol": wl["tol"], "l2": "256 MiB buffer written between timed steps"},
+                       "N_q": wl["n_q"], "tol": wl["tol"], "mode": mode,
+                       "l2": "256 MiB buffer written between timed steps"},
             "clocks": clocks, "kernels_one_step": kt,
             "solver": {"iterations": st["iterations"], "converged": st["converged"], "spectrum": spec}}
     ctx.close()

@@ -716,7 +716,8 @@ int vjp_core(ov_ctx* ctx, double a_eta, double gsc, double fsc, bool gamma5_eta,
       cj[j] = c;
     }
     SolveOut so;
-    st = solve_nodes_soa(ctx, src2, 2, nc, zh, ch, make_double2(0, 0), sums, X, o, &so, s);
+    st = o.mode == OV_MODE_F32X2 ? solve_nodes_soa_df(ctx, src2, 2, nc, zh, ch, make_double2(0, 0), sums, X, o, &so, s)
+                                 : solve_nodes_soa(ctx, src2, 2, nc, zh, ch, make_double2(0, 0), sums, X, o, &so, s);
     if (st != OV_OK && st != OV_ERR_NOT_CONVERGED) return st;
     if (st == OV_ERR_NOT_CONVERGED) tot.converged = 0;
     tot.iterations += so.iterations;

@@ -214,6 +214,10 @@ int solve_sign_soa(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nrhs
 int solve_nodes_soa(ov_ctx* ctx, const double2* b_soa, int nsrc, int ns, const std::vector<double2>& zh,
                     const std::vector<double2>& ch, double2 c0, double2* out_soa, double2* xs_soa,
                     const ov_solve_opts& o, SolveOut* so, cudaStream_t s);
+// The same with double-float vectors (OV_MODE_F32X2); xs_soa receives FP64 copies.
+int solve_nodes_soa_df(ov_ctx* ctx, const double2* b_soa, int nsrc, int ns, const std::vector<double2>& zh,
+                    const std::vector<double2>& ch, double2 c0, double2* out_soa, double2* xs_soa,
+                    const ov_solve_opts& o, SolveOut* so, cudaStream_t s);
 
 // coefficient-space Lanczos (OV_MODE_FP64_2PASS / _REGEN in FP64, OV_MODE_F32X2 in
 // double-float arithmetic)

@@ -115,6 +115,25 @@ struct SolveParams {
   int store;       // 1: slot i holds U_i for every i (basis kept for a later combination)
 };
 
+// Per-node coefficients l_{i-1}, c_j zeta_i, zeta_i of the vector-space update, stored
+// per iteration by K1's last block: FP64 for FP64 and FP32 vectors (converted where
+// used), double-float splits for double-float vectors (no per-element FP64 conversion).
+template <typename R>
+struct Coef {
+  using T = double2;
+  __device__ __forceinline__ static T make(double2 v) { return v; }
+  __device__ __forceinline__ static Cx<R> get(const T* p) {
+    const double2 v = __ldg(p);
+    return {(R)v.x, (R)v.y};
+  }
+};
+template <>
+struct Coef<DF> {
+  using T = float4;
+  __device__ __forceinline__ static T make(double2 v) { return Store<DF>::pack(cx_from<DF>(v.x, v.y)); }
+  __device__ __forceinline__ static Cx<DF> get(const T* p) { return Store<DF>::unpack(__ldg(p)); }
+};
+
 // Device pointers of one solve (all in workspace owned by the context).
 template <typename R>
 struct SolveArgs {
@@ -130,9 +149,9 @@ struct SolveArgs {
   const double2* z;   // [src][nshift]
   const double2* c;   // [src][nshift]
   int* act_idx;       // [src][nshift]
-  double2* act_l;     // [src][nshift] l_{i-1}
-  double2* act_cz;    // [src][nshift] c_j zeta_i
-  double2* act_z;     // [src][nshift] zeta_i
+  typename Coef<R>::T* act_l;   // [src][nshift] l_{i-1}
+  typename Coef<R>::T* act_cz;  // [src][nshift] c_j zeta_i
+  typename Coef<R>::T* act_z;   // [src][nshift] zeta_i
   double* part1;      // [src][nblk1]
   double* part2;      // [src][nblk2]
   unsigned* cnt;      // [src][2]
@@ -398,9 +417,9 @@ __global__ void __launch_bounds__(NT1, k1_min_blocks<R>()) lanczos_hw_kernel(Sol
     if (act) {
       const size_t o = (size_t)r * ns + na + slot;
       a.act_idx[o] = j;
-      a.act_l[o] = lprev;
-      a.act_cz[o] = cmul(a.c[(size_t)r * ns + j], zeta);
-      a.act_z[o] = zeta;
+      a.act_l[o] = Coef<R>::make(lprev);
+      a.act_cz[o] = Coef<R>::make(cmul(a.c[(size_t)r * ns + j], zeta));
+      a.act_z[o] = Coef<R>::make(zeta);
     }
     na += cnt;
   }
@@ -438,35 +457,36 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
     const Cx<R> u = lz_next<R>(ld<R>(W + e), v, alphaR);
     st<R>(W + e, u);
     nrm = Acc<R>::dot(nrm, u, u);
-    double sre = 0.0, sim = 0.0;
+    double sre = 0.0, sim = 0.0;      // weighted sum over nodes: FP64 (FP64, FP32 vectors)
+    Cx<R> sdf = {R(0), R(0)};          // or double-float (double-float vectors)
     const int* idx = a.act_idx + (size_t)r * ns;
-    const double2* al = a.act_l + (size_t)r * ns;
-    const double2* acz = a.act_cz + (size_t)r * ns;
-    const double2* az = a.act_z + (size_t)r * ns;
+    const typename Coef<R>::T* al = a.act_l + (size_t)r * ns;
+    const typename Coef<R>::T* acz = a.act_cz + (size_t)r * ns;
+    const typename Coef<R>::T* az = a.act_z + (size_t)r * ns;
     for (int k = 0; k < na; ++k) {
       const int j = __ldg(idx + k);
       T* P = a.p + ((size_t)r * ns + j) * n12 + e;
       Cx<R> pv = v;
-      if (i > 1) {
-        const double2 l = __ldg(al + k);
-        const Cx<R> po = ld<R>(P);
-        pv.re = v.re - ((R)l.x * po.re - (R)l.y * po.im);
-        pv.im = v.im - ((R)l.x * po.im + (R)l.y * po.re);
-      }
+      if (i > 1) pv = cfma(cneg(Coef<R>::get(al + k)), ld<R>(P), v);  // v - l p
       st<R>(P, pv);
-      const double2 cz = __ldg(acz + k);
-      sre += cz.x * (double)pv.re - cz.y * (double)pv.im;
-      sim += cz.x * (double)pv.im + cz.y * (double)pv.re;
+      if constexpr (std::is_same<R, DF>::value) {
+        sdf = cfma(Coef<R>::get(acz + k), pv, sdf);
+      } else {
+        const double2 cz = __ldg(acz + k);
+        sre += cz.x * (double)pv.re - cz.y * (double)pv.im;
+        sim += cz.x * (double)pv.im + cz.y * (double)pv.re;
+      }
       if (a.x) {
-        const double2 zt = __ldg(az + k);
         T* X = a.x + ((size_t)r * ns + j) * n12 + e;
-        Cx<R> xo = (i > 1) ? ld<R>(X) : Cx<R>{R(0), R(0)};
-        xo.re += (R)zt.x * pv.re - (R)zt.y * pv.im;
-        xo.im += (R)zt.x * pv.im + (R)zt.y * pv.re;
-        st<R>(X, xo);
+        const Cx<R> xo = (i > 1) ? ld<R>(X) : Cx<R>{R(0), R(0)};
+        st<R>(X, cfma(Coef<R>::get(az + k), pv, xo));
       }
     }
     if (a.sacc && na > 0) {
+      if constexpr (std::is_same<R, DF>::value) {
+        sre = (double)sdf.re;
+        sim = (double)sdf.im;
+      }
       double2* Sx = a.sacc + (size_t)r * n12 + e;
       double2 sv = *Sx;
       sv.x += sre;
@@ -1048,7 +1068,7 @@ int capture_groups(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, int G, F body, cu
 
 template <typename R>
 int setup_ws(ov_ctx* ctx, int nsrc, int ns, bool want_x, bool want_sacc, bool want_hist, int max_iter,
-             SolveWs<R>* w, const char* tag, int nslots = 3) {
+             SolveWs<R>* w, const char* tag, int nslots = 3, bool want_p = true) {
   using T = typename Store<R>::T;
   const int V = ctx->g.V;
   const size_t n12 = (size_t)12 * V;
@@ -1067,7 +1087,8 @@ int setup_ws(ov_ctx* ctx, int nsrc, int ns, bool want_x, bool want_sacc, bool wa
   auto& a = w->a;
   w->nslots = nslots;
   a.ring = (T*)ws_get(ctx, (t + ".ring").c_str(), sizeof(T) * (size_t)nslots * n12 * nsrc, &st);
-  a.p = ns ? (T*)ws_get(ctx, (t + ".p").c_str(), sizeof(T) * n12 * (size_t)nsrc * ns, &st) : nullptr;
+  // per-node direction vectors: only the vector-space form (coefficient-space: none)
+  a.p = (ns && want_p) ? (T*)ws_get(ctx, (t + ".p").c_str(), sizeof(T) * n12 * (size_t)nsrc * ns, &st) : nullptr;
   a.x = (want_x && ns) ? (T*)ws_get(ctx, (t + ".x").c_str(), sizeof(T) * n12 * (size_t)nsrc * ns, &st) : nullptr;
   a.sacc = want_sacc ? (double2*)ws_get(ctx, (t + ".sacc").c_str(), sizeof(double2) * n12 * nsrc, &st) : nullptr;
   a.src = (SrcState*)ws_get(ctx, (t + ".src").c_str(), sizeof(SrcState) * nsrc, &st);
@@ -1076,9 +1097,10 @@ int setup_ws(ov_ctx* ctx, int nsrc, int ns, bool want_x, bool want_sacc, bool wa
   a.z = (const double2*)ws_get(ctx, (t + ".z").c_str(), sizeof(double2) * nsh, &st);
   a.c = (const double2*)ws_get(ctx, (t + ".c").c_str(), sizeof(double2) * nsh, &st);
   a.act_idx = (int*)ws_get(ctx, (t + ".aidx").c_str(), sizeof(int) * nsh, &st);
-  a.act_l = (double2*)ws_get(ctx, (t + ".al").c_str(), sizeof(double2) * nsh, &st);
-  a.act_cz = (double2*)ws_get(ctx, (t + ".acz").c_str(), sizeof(double2) * nsh, &st);
-  a.act_z = (double2*)ws_get(ctx, (t + ".az").c_str(), sizeof(double2) * nsh, &st);
+  using CT = typename Coef<R>::T;
+  a.act_l = (CT*)ws_get(ctx, (t + ".al").c_str(), sizeof(CT) * nsh, &st);
+  a.act_cz = (CT*)ws_get(ctx, (t + ".acz").c_str(), sizeof(CT) * nsh, &st);
+  a.act_z = (CT*)ws_get(ctx, (t + ".az").c_str(), sizeof(CT) * nsh, &st);
   a.part1 = (double*)ws_get(ctx, (t + ".part1").c_str(), sizeof(double) * (size_t)w->nblk1 * nsrc, &st);
   a.part2 = (double*)ws_get(ctx, (t + ".part2").c_str(), sizeof(double) * (size_t)w->nblk2 * nsrc, &st);
   a.cnt = (unsigned*)ws_get(ctx, (t + ".cnt").c_str(), sizeof(unsigned) * 2 * nsrc, &st);
@@ -1273,25 +1295,59 @@ int finish_solve(ov_ctx* ctx, SolveWs<R>& w, int nsrc, int ns, const std::vector
 // Shifted FP64 solve with an explicit node list per source (zh, ch: nsrc x ns): the
 // weighted sum c0 b + sum_j c_j y_j goes to out_soa (if not null) and, if xs_soa is
 // not null, every node's solution y_j to xs_soa[src][j][12V].
-int solve_nodes_soa(ov_ctx* ctx, const double2* b_soa, int nsrc, int ns, const std::vector<double2>& zh,
-                    const std::vector<double2>& ch, double2 c0, double2* out_soa, double2* xs_soa,
-                    const ov_solve_opts& o, SolveOut* so, cudaStream_t s) {
-  SolveWs<double> w;
-  int st = setup_ws<double>(ctx, nsrc, ns, xs_soa != nullptr, true, false, o.max_iter, &w, "fp64");
+// The vector-space shifted solve for explicit nodes (per source), optionally keeping every
+// node's solution (xs, in the vector storage type): FP64 or double-float vectors.
+template <typename R>
+static int solve_nodes_t(ov_ctx* ctx, const double2* b_soa, int nsrc, int ns, const std::vector<double2>& zh,
+                         const std::vector<double2>& ch, double2 c0, double2* out_soa, typename Store<R>::T* xs,
+                         const ov_solve_opts& o, SolveOut* so, cudaStream_t s, const char* tag) {
+  SolveWs<R> w;
+  int st = setup_ws<R>(ctx, nsrc, ns, false, true, false, o.max_iter, &w, tag);
   if (st != OV_OK) return st;
-  if (xs_soa) w.a.x = xs_soa;
-  st = init_solve<double>(ctx, w, b_soa, nsrc, ns, zh, ch, c0, o.tol, o.max_iter, s);
+  w.a.x = xs;
+  st = init_solve<R>(ctx, w, b_soa, nsrc, ns, zh, ch, c0, o.tol, o.max_iter, s);
   if (st != OV_OK) return st;
-  double launches = 1.0 + (xs_soa ? 1.0 : 0.0);  // init (+ zeroing)
-  st = run_iterations<double>(ctx, w, nsrc, ns, xs_soa ? 1 : 0, o.max_iter, o, s, &launches);
+  double launches = 1.0 + (xs ? 1.0 : 0.0);  // init (+ zeroing)
+  st = run_iterations<R>(ctx, w, nsrc, ns, xs ? 1 : 0, o.max_iter, o, s, &launches);
   if (st != OV_OK) return st;
-  st = finish_solve<double>(ctx, w, nsrc, ns, zh, ch, so, s);
+  st = finish_solve<R>(ctx, w, nsrc, ns, zh, ch, so, s);
   so->launches = launches + 2.0;  // pack + unpack/epilogue issued by the caller
   if (out_soa) {
     // the weighted sum, even when not converged (best iterate)
     cudaError_t e = cudaMemcpyAsync(out_soa, w.a.sacc, sizeof(double2) * 12 * (size_t)ctx->g.V * nsrc,
                                     cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy sum");
+  }
+  return st;
+}
+
+int solve_nodes_soa(ov_ctx* ctx, const double2* b_soa, int nsrc, int ns, const std::vector<double2>& zh,
+                    const std::vector<double2>& ch, double2 c0, double2* out_soa, double2* xs_soa,
+                    const ov_solve_opts& o, SolveOut* so, cudaStream_t s) {
+  return solve_nodes_t<double>(ctx, b_soa, nsrc, ns, zh, ch, c0, out_soa, xs_soa, o, so, s, "fp64");
+}
+
+namespace {
+__global__ void df_to_double_kernel(const float4* __restrict__ in, double2* __restrict__ out, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const float4 v = in[t];
+    out[t] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+  }
+}
+}  // namespace
+
+int solve_nodes_soa_df(ov_ctx* ctx, const double2* b_soa, int nsrc, int ns, const std::vector<double2>& zh,
+                       const std::vector<double2>& ch, double2 c0, double2* out_soa, double2* xs_soa,
+                       const ov_solve_opts& o, SolveOut* so, cudaStream_t s) {
+  int st = ensure_links_df(ctx, s);
+  if (st != OV_OK) return st;
+  const size_t nx = (size_t)12 * ctx->g.V * nsrc * ns;
+  float4* xd = xs_soa ? (float4*)ws_get(ctx, "dfn.xs", sizeof(float4) * nx, &st) : nullptr;
+  if (st != OV_OK) return st;
+  st = solve_nodes_t<DF>(ctx, b_soa, nsrc, ns, zh, ch, c0, out_soa, xd, o, so, s, "dfn");
+  if (xs_soa && (st == OV_OK || st == OV_ERR_NOT_CONVERGED)) {
+    df_to_double_kernel<<<152 * 8, 256, 0, s>>>(xd, xs_soa, nx);
+    OV_CHECK_LAUNCH(ctx, "df_to_double_kernel");
   }
   return st;
 }
@@ -1358,7 +1414,7 @@ static int solve_sign_stored(ov_ctx* ctx, const double2* b_soa, double2* out_soa
   const size_t n12 = (size_t)12 * ctx->g.V;
   SolveWs<R> w;
   const std::string tag = std::string(coef_tag<R>()) + "s";
-  int st = setup_ws<R>(ctx, nsrc, ns, false, true, true, cap, &w, tag.c_str(), cap + 3);
+  int st = setup_ws<R>(ctx, nsrc, ns, false, true, true, cap, &w, tag.c_str(), cap + 3, false);
   if (st != OV_OK) return st;
   std::vector<double2> zh((size_t)nsrc * ns), ch((size_t)nsrc * ns);
   for (int r = 0; r < nsrc; ++r)
@@ -1501,7 +1557,7 @@ static int solve_sign_regen(ov_ctx* ctx, const double2* b_soa, double2* out_soa,
   const int ns = (int)ctx->z.size();
   SolveWs<R> w;
   const std::string tag = coef_tag<R>();
-  int st = setup_ws<R>(ctx, nsrc, ns, false, true, true, o.max_iter, &w, tag.c_str());
+  int st = setup_ws<R>(ctx, nsrc, ns, false, true, true, o.max_iter, &w, tag.c_str(), 3, false);
   if (st != OV_OK) return st;
   double2* gco = (double2*)ws_get(ctx, (tag + ".gco").c_str(), sizeof(double2) * (size_t)nsrc * o.max_iter, &st);
   if (st != OV_OK) return st;
@@ -1665,7 +1721,7 @@ int solve_sign_mixed(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int ns
       ch[(size_t)r * nq + j] = ctx->c[j];
     }
   SolveWs<float> wA;
-  st = setup_ws<float>(ctx, nsrc, nq, false, false, true, kcap, &wA, "mxA", kcap + 2);
+  st = setup_ws<float>(ctx, nsrc, nq, false, false, true, kcap, &wA, "mxA", kcap + 2, false);
   if (st != OV_OK) return st;
   const double tolA = std::max(o.tol, 1e-6);
   st = init_solve<float>(ctx, wA, b_soa, nsrc, nq, zh, ch, make_double2(0, 0), tolA, kcap, s, 0);

@@ -141,3 +141,12 @@ def test_autograd_function(gpu_lib):
         Lm = torch.real(torch.vdot(eta.reshape(-1), ops.sgn_apply(ctx, b - h * d, opts).reshape(-1)))
     fd = float((Lp - Lm) / (2 * h))
     assert abs(fd - float(torch.real(torch.vdot(b.grad.reshape(-1), d.reshape(-1))))) < 1e-7 * abs(fd)
+
+
+def test_double_float_vjp_matches_fp64(gpu_lib, config4):
+    """The gradient with double-float vectors (mode f32x2) equals the FP64 one to 1e-10,
+    and the force still matches a central finite difference."""
+    ctx, U, b, eta, gb, F, st = config4
+    gb2, F2, st2 = _vjp(gpu_lib, ctx, eta, b, mode="f32x2")
+    assert rel(gb2, gb) < 1e-10
+    assert np.abs(F2 - F).max() <= 1e-10 * np.abs(F).max()
