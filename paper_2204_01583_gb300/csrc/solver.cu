@@ -46,10 +46,10 @@ namespace {
 constexpr int NT1 = 128;  // K1: stencil + Lanczos epilogue; K3: regeneration pass
 constexpr int NT2 = 256;  // K2: vector updates
 // Resident blocks per SM the stencil kernels are compiled for: 4 (<= 128 registers) for
-// FP64; 6 (<= 80 registers) for double-float, whose stencil is issue-bound
-// and gains from the extra warps.
+// FP64; 8 (<= 64 registers) for double-float, whose stencil gains from
+// the extra warps (16^3x32, 12 sources: 766 / 744 / 734 us per launch at 6 / 7 / 8).
 template <typename R>
-constexpr int k1_min_blocks() { return std::is_same<R, DF>::value ? 6 : 4; }
+constexpr int k1_min_blocks() { return std::is_same<R, DF>::value ? 8 : 4; }
 
 struct SrcState {
   double bnorm;   // ||b||
