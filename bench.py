@@ -65,7 +65,7 @@ WORKLOADS = {
                                     inner_tol=1e-12, mode="f32x2", kind="ovsolve"),
     # gradient of Re<eta, sgn(H_W) b> w.r.t. b and the links (adjoint solves + fused force)
     "vjp-8^4-nq48": dict(dims=(8, 8, 8, 8), eps=0.4, n_q=48, nsrc=1, src="gauss", tol=1e-12, kind="vjp",
-                         mode="fp64"),
+                         mode="f32x2"),
     # the same measure with Zolotarev's optimal node set (n pole pairs = 2n nodes) from Lanczos bounds
     "sigma-8^4-zolotarev": dict(dims=(8, 8, 8, 8), eps=0.5, nsrc=4, src="gauss", kind="sigma", rule="zolotarev",
                                 n_list=(4, 8, 12, 16, 20)),

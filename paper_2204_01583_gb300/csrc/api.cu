@@ -703,7 +703,36 @@ int vjp_core(ov_ctx* ctx, double a_eta, double gsc, double fsc, bool gamma5_eta,
   cudaMemsetAsync(F, 0, sizeof(double) * 32 * (size_t)V, s);
   SolveOut tot;
   tot.converged = 1;
-  for (int j0 = 0; j0 < nq; j0 += chunk) {
+  // Coefficient-space forms: one stored-basis Lanczos pass for both sources, per-node
+  // solutions formed from the basis chunk by chunk (no repeated solves).  Falls back to the
+  // vector-space form when the basis does not fit.
+  bool coef_done = false;
+  if (o.mode == OV_MODE_FP64_2PASS || o.mode == OV_MODE_FP64_REGEN || o.mode == OV_MODE_F32X2) {
+    std::vector<double2> zh(2 * (size_t)nq), ch(2 * (size_t)nq);
+    for (int j = 0; j < nq; ++j) {
+      const double2 z = ctx->z[j], c = ctx->c[j];
+      zh[j] = z;
+      ch[j] = c;
+      zh[nq + j] = make_double2(z.x, -z.y);
+      ch[nq + j] = make_double2(c.x, -c.y);
+    }
+    auto force_chunk = [&](int j0, int nc) -> int {
+      if (!grad_links) return OV_OK;
+      cudaError_t e = cudaMemcpyAsync(cq, ctx->c.data() + j0, sizeof(double2) * nc, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy coefficients");
+      return launch_force(ctx, X, nc, cq, F, s);
+    };
+    SolveOut so;
+    st = solve_nodes_coef(ctx, src2, 2, nq, zh, ch, chunk, X, sums, o, &so, s, force_chunk);
+    if (st == OV_OK || st == OV_ERR_NOT_CONVERGED) {
+      coef_done = true;
+      tot = so;
+      axpy_c_kernel<<<512, 256, 0, s>>>(gb, sums + n12, make_double2(gsc, 0.0), n12);
+    } else if (st != OV_ERR_INVALID_ARG) {
+      return st;
+    }
+  }
+  for (int j0 = 0; j0 < nq && !coef_done; j0 += chunk) {
     const int nc = std::min(chunk, nq - j0);
     // source 0 (b): nodes z_j; source 1 (eta_s): nodes conj(z_j), coefficients conj(c_j)
     std::vector<double2> zh(2 * (size_t)nc), ch(2 * (size_t)nc), cj(nc);

@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -214,6 +215,13 @@ int solve_sign_soa(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nrhs
 int solve_nodes_soa(ov_ctx* ctx, const double2* b_soa, int nsrc, int ns, const std::vector<double2>& zh,
                     const std::vector<double2>& ch, double2 c0, double2* out_soa, double2* xs_soa,
                     const ov_solve_opts& o, SolveOut* so, cudaStream_t s);
+// Per-node solutions X[src][node][12V] (FP64) of explicit per-source node lists through a
+// stored Lanczos basis (FP64, or double-float for OV_MODE_F32X2), chunk nodes at a time
+// (per_chunk(j0, nc) runs after each chunk), and the weighted sums sum_j c_j x_j into
+// sums[src][12V].  OV_ERR_INVALID_ARG: the basis does not fit (use solve_nodes_soa).
+int solve_nodes_coef(ov_ctx* ctx, const double2* b_soa, int nsrc, int ns, const std::vector<double2>& zh,
+                     const std::vector<double2>& ch, int chunk, double2* X, double2* sums, const ov_solve_opts& o,
+                     SolveOut* so, cudaStream_t s, const std::function<int(int, int)>& per_chunk);
 // The same with double-float vectors (OV_MODE_F32X2); xs_soa receives FP64 copies.
 int solve_nodes_soa_df(ov_ctx* ctx, const double2* b_soa, int nsrc, int ns, const std::vector<double2>& zh,
                     const std::vector<double2>& ch, double2 c0, double2* out_soa, double2* xs_soa,

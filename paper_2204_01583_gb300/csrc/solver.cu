@@ -34,6 +34,7 @@
 #include <cstdio>
 #include <string>
 #include <cstring>
+#include <functional>
 #include <type_traits>
 #include <vector>
 
@@ -846,6 +847,34 @@ __global__ void basis_sum_kernel(const typename Store<R>::T* __restrict__ basis,
   sv.x += (double)acc.re;
   sv.y += (double)acc.im;
   sum[(size_t)r * n12 + e] = sv;
+}
+
+// Per-node solutions from a stored basis: X[r][jj][e] = sum_{i=1..k_r} Y[r][j0 + jj][i-1] U_i[e]
+// for the nc nodes of a chunk (Y holds the FOM coefficients folded with 1 / ||U_i||), JT
+// nodes per thread so that one read of the basis serves JT outputs; FP64 output.
+template <typename R, int JT>
+__global__ void basis_nodes_kernel(const typename Store<R>::T* __restrict__ basis, int nslots,
+                                   const typename Store<R>::T* __restrict__ Y, int ns, int ldy,
+                                   const int* __restrict__ kr, int j0, int nc, double2* __restrict__ X,
+                                   size_t n12) {
+  const int r = blockIdx.y, jt = blockIdx.z * JT;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n12 || jt >= nc) return;
+  const typename Store<R>::T* B = basis + (size_t)r * nslots * n12 + e;
+  const typename Store<R>::T* Yr = Y + ((size_t)r * ns + j0 + jt) * ldy;
+  const int k = kr[r], nj = min(JT, nc - jt);
+  Cx<R> acc[JT];
+#pragma unroll
+  for (int q = 0; q < JT; ++q) acc[q] = {R(0), R(0)};
+  for (int i = 1; i <= k; ++i) {
+    const Cx<R> u = ld<R>(B + (size_t)i * n12);
+#pragma unroll
+    for (int q = 0; q < JT; ++q)
+      if (q < nj) acc[q] = cfma(ld<R>(Yr + (size_t)q * ldy + (i - 1)), u, acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < JT; ++q)
+    if (q < nj) X[((size_t)r * nc + jt + q) * n12 + e] = make_double2((double)acc[q].re, (double)acc[q].im);
 }
 
 // sum += (double) ssum: the double-float regeneration-pass sum into the FP64 sum
@@ -1675,6 +1704,119 @@ static int solve_sign_regen(ov_ctx* ctx, const double2* b_soa, double2* out_soa,
   e = cudaMemcpyAsync(out_soa, w.a.sacc, sizeof(double2) * n12 * nsrc, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy sum");
   return fst;
+}
+
+// Per-node solutions of explicit per-source node lists through the coefficient space:
+// one stored-basis Lanczos pass for all sources (no per-node vectors), the FOM coefficient
+// vector of every node on the host, then x_j = V y^j for one chunk of nodes at a time
+// (each chunk handed to per_chunk) and the weighted sums sum_j c_j x_j.  The Lanczos
+// work does not repeat per chunk.  Returns OV_ERR_INVALID_ARG when the basis does not fit
+// the store budget or the solve outgrows it (the caller uses the vector-space form).
+template <typename R>
+static int nodes_coef(ov_ctx* ctx, const double2* b_soa, int nsrc, int ns, const std::vector<double2>& zh,
+                      const std::vector<double2>& ch, int chunk, double2* X, double2* sums, const ov_solve_opts& o,
+                      SolveOut* so, cudaStream_t s, const std::function<int(int, int)>& per_chunk) {
+  const size_t n12 = (size_t)12 * ctx->g.V;
+  size_t freeb = 0, totalb = 0;
+  cudaMemGetInfo(&freeb, &totalb);
+  const std::string tag = std::string(coef_tag<R>()) + "s";
+  auto it = ctx->bufs.find(tag + ".ring");
+  const double held = it != ctx->bufs.end() ? (double)it->second.bytes : 0.0;
+  const double budget = std::min(0.40 * (double)totalb, (double)freeb + held - 0.10 * (double)totalb);
+  const int cap = std::min(o.max_iter, ctx->coef_iter_hint > 0 ? std::max(64, ctx->coef_iter_hint * 5 / 4 + 32) : 1024);
+  if ((double)(cap + 3) * nsrc * n12 * sizeof(double2) > budget) return OV_ERR_INVALID_ARG;
+  SolveWs<R> w;
+  int st = setup_ws<R>(ctx, nsrc, ns, false, true, true, cap, &w, tag.c_str(), cap + 3, false);
+  if (st != OV_OK) return st;
+  st = init_solve<R>(ctx, w, b_soa, nsrc, ns, zh, ch, make_double2(0.0, 0.0), o.tol, cap, s, 0);
+  if (st != OV_OK) return st;
+  double launches = 1.0;
+  st = run_iterations<R>(ctx, w, nsrc, ns, 7, cap, o, s, &launches);
+  if (st != OV_OK) return st;
+  const int fst = finish_solve<R>(ctx, w, nsrc, ns, zh, ch, so, s);
+  if (fst != OV_OK && !(fst == OV_ERR_NOT_CONVERGED && cap >= o.max_iter)) return OV_ERR_INVALID_ARG;
+  std::vector<SrcState> S(nsrc);
+  std::vector<double> ha((size_t)nsrc * cap), hb((size_t)nsrc * cap);
+  cudaError_t e = cudaMemcpyAsync(S.data(), w.a.src, sizeof(SrcState) * nsrc, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ha.data(), w.a.hist_a, sizeof(double) * ha.size(), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), w.a.hist_b, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "read Lanczos history");
+  // FOM coefficients y^j = (z_j - T_k)^-1 e_1 ||b|| per source and node (forward LDL^T sweep,
+  // back substitution), folded with 1 / ||U_i||; g_r = sum_j c_j y^j for the sums
+  using T = typename Store<R>::T;
+  std::vector<T> Yh((size_t)nsrc * ns * cap);
+  std::vector<T> gh((size_t)nsrc * cap);
+  std::vector<int> kr(nsrc);
+  std::vector<std::complex<double>> dd, ll, zt, yy, gs;
+  for (int r = 0; r < nsrc; ++r) {
+    const int k = kr[r] = std::max(0, S[r].iter - 1);
+    const double* al = ha.data() + (size_t)r * cap;
+    const double* be = hb.data() + (size_t)r * cap;
+    dd.assign(k, 0.0);
+    ll.assign(k, 0.0);
+    zt.assign(k, 0.0);
+    yy.assign(k, 0.0);
+    gs.assign(k, 0.0);
+    for (int j = 0; j < ns && k > 0; ++j) {
+      const std::complex<double> zj(zh[(size_t)r * ns + j].x, zh[(size_t)r * ns + j].y);
+      const std::complex<double> cj(ch[(size_t)r * ns + j].x, ch[(size_t)r * ns + j].y);
+      std::complex<double> om = S[r].bnorm;
+      for (int i = 0; i < k; ++i) {
+        if (i == 0) {
+          dd[0] = zj - al[0];
+        } else {
+          dd[i] = zj - al[i] - be[i - 1] * be[i - 1] / dd[i - 1];
+          om = -ll[i - 1] * om;
+        }
+        ll[i] = -be[i] / dd[i];
+        zt[i] = om / dd[i];
+      }
+      yy[k - 1] = zt[k - 1];
+      for (int i = k - 2; i >= 0; --i) yy[i] = zt[i] - ll[i] * yy[i + 1];
+      for (int i = 0; i < k; ++i) {
+        const double ni = (i == 0) ? S[r].bnorm : be[i - 1];
+        const std::complex<double> y = yy[i] / ni;
+        Yh[((size_t)r * ns + j) * cap + i] = host_store(make_double2(y.real(), y.imag()), (T*)nullptr);
+        gs[i] += cj * y;
+      }
+    }
+    for (int i = 0; i < k; ++i) gh[(size_t)r * cap + i] = host_store(make_double2(gs[i].real(), gs[i].imag()), (T*)nullptr);
+  }
+  T* Yd = (T*)ws_get(ctx, (tag + ".Y").c_str(), sizeof(T) * Yh.size(), &st);
+  T* gd = (T*)ws_get(ctx, (tag + ".g").c_str(), sizeof(T) * gh.size(), &st);
+  int* krd = (int*)ws_get(ctx, (tag + ".kr").c_str(), sizeof(int) * nsrc, &st);
+  if (st != OV_OK) return st;
+  e = cudaMemcpyAsync(Yd, Yh.data(), sizeof(T) * Yh.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(gd, gh.data(), sizeof(T) * gh.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(krd, kr.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sums, 0, sizeof(double2) * n12 * nsrc, s);
+  if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy node coefficients");
+  basis_sum_kernel<R><<<dim3((unsigned)((n12 + 255) / 256), nsrc), 256, 0, s>>>(w.a.ring, cap + 3, gd, cap, krd,
+                                                                             sums, n12);
+  OV_CHECK_LAUNCH(ctx, "basis_sum_kernel");
+  constexpr int JT = 8;
+  for (int j0 = 0; j0 < ns; j0 += chunk) {
+    const int nc = std::min(chunk, ns - j0);
+    basis_nodes_kernel<R, JT><<<dim3((unsigned)((n12 + 255) / 256), nsrc, (nc + JT - 1) / JT), 256, 0, s>>>(
+        w.a.ring, cap + 3, Yd, ns, cap, krd, j0, nc, X, n12);
+    OV_CHECK_LAUNCH(ctx, "basis_nodes_kernel");
+    if ((st = per_chunk(j0, nc)) != OV_OK) return st;
+  }
+  so->launches = launches + 2.0 + (ns + chunk - 1) / chunk;
+  if (so->converged) ctx->coef_iter_hint = so->iterations;
+  return fst;
+}
+
+int solve_nodes_coef(ov_ctx* ctx, const double2* b_soa, int nsrc, int ns, const std::vector<double2>& zh,
+                     const std::vector<double2>& ch, int chunk, double2* X, double2* sums, const ov_solve_opts& o,
+                     SolveOut* so, cudaStream_t s, const std::function<int(int, int)>& per_chunk) {
+  if (o.mode == OV_MODE_F32X2) {
+    const int st = ensure_links_df(ctx, s);
+    if (st != OV_OK) return st;
+    return nodes_coef<DF>(ctx, b_soa, nsrc, ns, zh, ch, chunk, X, sums, o, so, s, per_chunk);
+  }
+  return nodes_coef<double>(ctx, b_soa, nsrc, ns, zh, ch, chunk, X, sums, o, so, s, per_chunk);
 }
 
 int solve_sign_2pass(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc, const ov_solve_opts& o,

@@ -143,10 +143,11 @@ def test_autograd_function(gpu_lib):
     assert abs(fd - float(torch.real(torch.vdot(b.grad.reshape(-1), d.reshape(-1))))) < 1e-7 * abs(fd)
 
 
-def test_double_float_vjp_matches_fp64(gpu_lib, config4):
-    """The gradient with double-float vectors (mode f32x2) equals the FP64 one to 1e-10,
-    and the force still matches a central finite difference."""
+@pytest.mark.parametrize("mode,chunk", [("fp64_2pass", 0), ("fp64_2pass", 7), ("f32x2", 0), ("f32x2", 13)])
+def test_coefficient_space_vjp_matches_vector_space(gpu_lib, config4, mode, chunk):
+    """The gradient through a stored Lanczos basis (per-node solutions formed from it, chunk
+    by chunk; FP64 or double-float vectors) equals the FP64 vector-space one to 1e-10."""
     ctx, U, b, eta, gb, F, st = config4
-    gb2, F2, st2 = _vjp(gpu_lib, ctx, eta, b, mode="f32x2")
+    gb2, F2, st2 = _vjp(gpu_lib, ctx, eta, b, mode=mode, node_chunk=chunk)
     assert rel(gb2, gb) < 1e-10
     assert np.abs(F2 - F).max() <= 1e-10 * np.abs(F).max()
