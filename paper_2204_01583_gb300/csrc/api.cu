@@ -298,9 +298,52 @@ int ov_set_gauge(ov_ctx* ctx, const double* U, int on_device, void* stream) {
   ctx->coef_iter_hint = 0;
   ctx->have_c32 = false;
   ctx->have_b32 = false;
+  ctx->have_b12 = false;
   ctx->have_s4 = false;
   ctx->have_df = false;
   return OV_OK;
+}
+
+// FP32 stencil variants on float4 layouts, numbered after the structure-of-arrays ones:
+// layout P (right-hand-side pairs, 12 float4 per site and pair) or S (spin pairs, 6
+// float4 per site and RHS; its buffers alias the paired ones, 6 <= 12 per pair).
+struct Float4Variant {
+  bool paired;
+  int form;              // launch_hw_pair12 form, -1: broadcast-link kernel; S: launch_hw32_s4 comp
+  int rhs_tile, code, threads;  // as reported by ov_hw32_variants
+};
+constexpr Float4Variant kFloat4Variants[] = {
+    {true, -1, 2, 2, 128},  // P, broadcast 9-element links
+    {false, 0, 1, 3, 128},  // S, padded 5-float4 links
+    {false, 1, 1, 4, 128},  // S, 12-real links
+    {false, 2, 6, 5, 0},    // S, one xy-plane per block, links and plane staged in shared memory
+    {true, 0, 2, 6, 128},   // P, 12-real links stored broadcast
+    {true, 1, 2, 7, 128},   // P, 12-real links compact
+    {false, 3, 1, 8, 128},  // S, 12-real links, centre first
+    {false, 4, 1, 8, 256},  // S, 12-real links, centre first, 256 threads per block
+    {true, 2, 2, 9, 128},   // P, 12-real compact links, centre first
+    {true, 3, 2, 9, 256},   // P, the same with 256 threads per block
+    {true, 4, 2, 10, 128},  // P, all 9 link elements (padded 5 float4), centre first
+    {true, 5, 2, 11, 128},  // P, 12-real compact links, in-plane neighbours staged in shared memory
+    {true, 6, 2, 12, 128},  // P, 12-real compact links, centre first, row 2 rebuilt in scalar
+};
+constexpr int kNFloat4Variants = sizeof(kFloat4Variants) / sizeof(kFloat4Variants[0]);
+
+static int fp32_float4_pack(ov_ctx* ctx, int v, const float2* in, float4* buf, int nrhs, cudaStream_t s) {
+  return kFloat4Variants[v].paired ? launch_pack_pair32(ctx, in, buf, nrhs, s) : launch_pack_s4(ctx, in, buf, nrhs, s);
+}
+
+static int fp32_float4_unpack(ov_ctx* ctx, int v, const float4* buf, float2* out, int nrhs, cudaStream_t s) {
+  return kFloat4Variants[v].paired ? launch_unpack_pair32(ctx, buf, out, nrhs, s)
+                                   : launch_unpack_s4(ctx, buf, out, nrhs, s);
+}
+
+static int fp32_float4_launch(ov_ctx* ctx, int v, const float4* in, float4* out, int nrhs, cudaStream_t s) {
+  const Float4Variant& f = kFloat4Variants[v];
+  const int npair = (nrhs + 1) / 2;
+  if (!f.paired) return launch_hw32_s4(ctx, in, out, nrhs, f.form, s);
+  if (f.form < 0) return launch_hw_pair(ctx, in, out, npair, s);
+  return launch_hw_pair12(ctx, in, out, npair, f.form, s);
 }
 
 int ov_apply_HW(ov_ctx* ctx, const void* in, void* out, int nrhs, int precision, void* stream) {
@@ -323,53 +366,37 @@ int ov_apply_HW(ov_ctx* ctx, const void* in, void* out, int nrhs, int precision,
     if ((st = launch_unpack64(ctx, b, (double2*)out, nrhs, s))) return st;
   } else {
     const int npair = (nrhs + 1) / 2;
-    // then kpair + 1, kpair + 2: spin-paired float4 layout; kpair + 3: the same with one
-    // xy-plane per block and links staged in shared memory (lattices with Lx Ly = 32k <= 1024)
     const int kpair = hw32_variant_count();
     float2* a = (float2*)ws_get(ctx, "hw.a32", sizeof(float2) * n, &st);
     float2* b = (float2*)ws_get(ctx, "hw.b32", sizeof(float2) * n, &st);
     float4* pa = (float4*)ws_get(ctx, "hw.pa32", sizeof(float4) * 12 * (size_t)ctx->g.V * npair, &st);
     float4* pb = (float4*)ws_get(ctx, "hw.pb32", sizeof(float4) * 12 * (size_t)ctx->g.V * npair, &st);
     if (st != OV_OK) return st;
-    // the S4 buffers alias the paired ones (6 float4 per site and RHS <= 12 per pair)
-    float4* sa = pa;
-    float4* sb = pb;
     int k = ctx->hw32_force;
     if (k < 0) {
       auto it = ctx->hw32_choice.find(nrhs);
       if (it != ctx->hw32_choice.end()) {
         k = it->second;
       } else {
-        // autotune: every structure-of-arrays variant, the paired kernel and the S4
+        // autotune: every structure-of-arrays variant, then the paired and spin-paired
         // kernels, each timed on this data
         if ((st = launch_pack32(ctx, (const float2*)in, a, nrhs, s))) return st;
         int ksoa = 0;
-        const float soa_ms = hw32_time_soa_variants(ctx, a, b, nrhs, s, &ksoa);
-        float best = soa_ms;
+        float best = hw32_time_soa_variants(ctx, a, b, nrhs, s, &ksoa);
         k = ksoa;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        for (int kk = kpair; kk <= kpair + 3; ++kk) {
-          if (kk == kpair) {
-            if ((st = launch_pack_pair32(ctx, (const float2*)in, pa, nrhs, s))) return st;
-            if ((st = launch_hw_pair(ctx, pa, pb, npair, s))) return st;  // warm (builds the links)
-          } else {
-            if ((st = launch_pack_s4(ctx, (const float2*)in, sa, nrhs, s))) return st;
-            st = launch_hw32_s4(ctx, sa, sb, nrhs, kk - kpair - 1, s);
-            if (st == OV_ERR_INVALID_ARG) {  // this lattice does not fit the variant
-              st = OV_OK;
-              continue;
-            }
-            if (st != OV_OK) return st;
+        for (int kk = kpair; kk < kpair + kNFloat4Variants; ++kk) {
+          if ((st = fp32_float4_pack(ctx, kk - kpair, (const float2*)in, pa, nrhs, s))) return st;
+          st = fp32_float4_launch(ctx, kk - kpair, pa, pb, nrhs, s);  // warm (builds the links)
+          if (st == OV_ERR_INVALID_ARG) {  // this lattice does not fit the variant
+            st = OV_OK;
+            continue;
           }
+          if (st != OV_OK) return st;
           cudaEventRecord(e0, s);
-          for (int rep = 0; rep < 3; ++rep) {
-            if (kk == kpair)
-              launch_hw_pair(ctx, pa, pb, npair, s);
-            else
-              launch_hw32_s4(ctx, sa, sb, nrhs, kk - kpair - 1, s);
-          }
+          for (int rep = 0; rep < 3; ++rep) fp32_float4_launch(ctx, kk - kpair, pa, pb, nrhs, s);
           cudaEventRecord(e1, s);
           cudaEventSynchronize(e1);
           float ms = 0.f;
@@ -384,14 +411,10 @@ int ov_apply_HW(ov_ctx* ctx, const void* in, void* out, int nrhs, int precision,
         ctx->hw32_choice[nrhs] = k;
       }
     }
-    if (k == kpair) {
-      if ((st = launch_pack_pair32(ctx, (const float2*)in, pa, nrhs, s))) return st;
-      if ((st = launch_hw_pair(ctx, pa, pb, npair, s))) return st;
-      if ((st = launch_unpack_pair32(ctx, pb, (float2*)out, nrhs, s))) return st;
-    } else if (k > kpair) {
-      if ((st = launch_pack_s4(ctx, (const float2*)in, sa, nrhs, s))) return st;
-      if ((st = launch_hw32_s4(ctx, sa, sb, nrhs, k - kpair - 1, s))) return st;
-      if ((st = launch_unpack_s4(ctx, sb, (float2*)out, nrhs, s))) return st;
+    if (k >= kpair) {
+      if ((st = fp32_float4_pack(ctx, k - kpair, (const float2*)in, pa, nrhs, s))) return st;
+      if ((st = fp32_float4_launch(ctx, k - kpair, pa, pb, nrhs, s))) return st;
+      if ((st = fp32_float4_unpack(ctx, k - kpair, pb, (float2*)out, nrhs, s))) return st;
     } else {
       if ((st = launch_pack32(ctx, (const float2*)in, a, nrhs, s))) return st;
       if ((st = launch_hw32_tuned(ctx, a, b, nrhs, s, k, nullptr))) return st;
@@ -800,7 +823,7 @@ int ov_overlap_vjp(ov_ctx* ctx, double m_q, const void* eta, const void* b, void
 
 int ov_set_hw32_variant(ov_ctx* ctx, int k) {
   if (!ctx) return OV_ERR_INVALID_ARG;
-  if (k < -1 || k > hw32_variant_count() + 3) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "no such FP32 stencil variant");
+  if (k < -1 || k >= hw32_variant_count() + kNFloat4Variants) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "no such FP32 stencil variant");
   ctx->hw32_force = k;
   return OV_OK;
 }
@@ -808,16 +831,13 @@ int ov_set_hw32_variant(ov_ctx* ctx, int k) {
 int ov_hw32_variants(int k, int* rhs_tile, int* compressed, int* threads) {
   const int n = hw32_variant_count();
   if (k >= 0 && k < n && rhs_tile && compressed && threads) hw32_variant_info(k, rhs_tile, compressed, threads);
-  if (k >= n && k <= n + 3 && rhs_tile && compressed && threads) {
-    // n: right-hand-side-paired layout, paired FP32 instructions, broadcast links;
-    // n + 1, n + 2: spin-paired float4 layout with plain (padded) or 12-real links;
-    // n + 3: spin-paired layout, one xy-plane per block (Lx Ly threads), 12-real links and
-    // the plane's spinor staged in shared memory, 6 right-hand sides per block
-    *rhs_tile = (k == n) ? 2 : (k == n + 3 ? 6 : 1);
-    *compressed = 2 + (k - n);
-    *threads = (k == n + 3) ? 0 : 128;
+  if (k >= n && k < n + kNFloat4Variants && rhs_tile && compressed && threads) {
+    const Float4Variant& f = kFloat4Variants[k - n];
+    *rhs_tile = f.rhs_tile;
+    *compressed = f.code;
+    *threads = f.threads;
   }
-  return n + 4;
+  return n + kNFloat4Variants;
 }
 
 int ov_set_concurrency(ov_ctx* ctx, int groups) {

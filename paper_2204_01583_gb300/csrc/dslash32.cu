@@ -348,21 +348,40 @@ __device__ __forceinline__ void hop_dir_s4(const float4* __restrict__ in, const 
   }
 }
 
-// 7 resident blocks per SM (<= 72 registers): the kernel waits on L2 latency, and the
-// extra warps hide more of it (16^3x32, 12 RHS: 102.7 us at 80 registers, 97.3 us here)
-template <bool COMP, int NT>
-__global__ void __launch_bounds__(NT, 7) hw32_s4_kernel(const float4* __restrict__ in, float4* __restrict__ out,
-                                                     const float4* __restrict__ L, Geom g, float diag) {
+// 7 resident blocks of 128 threads per SM (<= 72 registers): the kernel waits on L2
+// latency, and the extra warps hide more of it (16^3x32, 12 RHS: 102.7 us at 80
+// registers, 97.3 us here).  CF (centre first): the diagonal term is read before the
+// hops, so that the x and y neighbours, which share its cache lines, follow it through L1.
+template <int NT>
+constexpr int s4_min_blocks() {
+  return NT == 128 ? 7 : 3;
+}
+
+template <bool COMP, int NT, bool CF>
+__global__ void __launch_bounds__(NT, s4_min_blocks<NT>()) hw32_s4_kernel(const float4* __restrict__ in,
+                                                                          float4* __restrict__ out,
+                                                                          const float4* __restrict__ L, Geom g,
+                                                                          float diag) {
   const int s = blockIdx.x * NT + threadIdx.x;
   if (s >= g.V) return;
+  int c[4];
+  site_coords(g, s, c);
   const int V = g.V;
   const float4* inr = in + (size_t)blockIdx.y * 6 * V;
   float4* outr = out + (size_t)blockIdx.y * 6 * V;
   Cx<float> acc[12];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) acc[k] = {0.f, 0.f};
-  int c[4];
-  site_coords(g, s, c);
+  for (int p = 0; p < 6; ++p) {
+    const int sp = p / 3, col = p % 3;
+    if (CF) {
+      const float4 v = __ldg(inr + p * V + s);
+      acc[sp * 3 + col] = cscale(diag, Cx<float>{v.x, v.y});
+      acc[(sp + 2) * 3 + col] = cscale(diag, Cx<float>{v.z, v.w});
+    } else {
+      acc[sp * 3 + col] = {0.f, 0.f};
+      acc[(sp + 2) * 3 + col] = {0.f, 0.f};
+    }
+  }
   hop_dir_s4<0, COMP>(inr, L, g, s, c, acc);
   hop_dir_s4<1, COMP>(inr, L, g, s, c, acc);
   hop_dir_s4<2, COMP>(inr, L, g, s, c, acc);
@@ -370,11 +389,14 @@ __global__ void __launch_bounds__(NT, 7) hw32_s4_kernel(const float4* __restrict
 #pragma unroll
   for (int p = 0; p < 6; ++p) {
     const int sp = p / 3, col = p % 3;
-    const float4 v = __ldg(inr + p * V + s);
+    Cx<float> up = acc[sp * 3 + col], lo = acc[(sp + 2) * 3 + col];
+    if (!CF) {
+      const float4 v = __ldg(inr + p * V + s);
+      up = cadd(cscale(diag, Cx<float>{v.x, v.y}), up);
+      lo = cadd(cscale(diag, Cx<float>{v.z, v.w}), lo);
+    }
     // upper spin sp, lower spin sp + 2 (gamma5 = -1 on it)
-    const Cx<float> up = cadd(cscale(diag, Cx<float>{v.x, v.y}), acc[sp * 3 + col]);
-    const Cx<float> lo = cneg(cadd(cscale(diag, Cx<float>{v.z, v.w}), acc[(sp + 2) * 3 + col]));
-    outr[p * V + s] = make_float4(up.re, up.im, lo.re, lo.im);
+    outr[p * V + s] = make_float4(up.re, up.im, -lo.re, -lo.im);
   }
 }
 
@@ -564,16 +586,27 @@ int launch_unpack_s4(ov_ctx* ctx, const float4* s4, float2* aos, int nrhs, cudaS
   return OV_OK;
 }
 
-// out = H_W in on the S4 layout; comp selects the 3-float4 (compressed) links.
-int launch_hw32_s4(ov_ctx* ctx, const float4* in, float4* out, int nrhs, int comp, cudaStream_t s) {
-  int st = OV_OK;
-  float4* l5 = (float4*)ws_get(ctx, "gauge.s4l5", sizeof(float4) * 4 * 5 * (size_t)ctx->g.V, &st);
-  float4* l3 = (float4*)ws_get(ctx, "gauge.s4l3", sizeof(float4) * 4 * 3 * (size_t)ctx->g.V, &st);
-  if (st != OV_OK) return st;
+// The S4 link forms (built together on first use after set_gauge): comp = true gives
+// the 3-float4 (12-real) links, false the 5-float4 (padded pairs) links.
+const float4* s4_links(ov_ctx* ctx, bool comp, cudaStream_t s, int* st) {
+  float4* l5 = (float4*)ws_get(ctx, "gauge.s4l5", sizeof(float4) * 4 * 5 * (size_t)ctx->g.V, st);
+  float4* l3 = (float4*)ws_get(ctx, "gauge.s4l3", sizeof(float4) * 4 * 3 * (size_t)ctx->g.V, st);
+  if (*st != OV_OK) return nullptr;
   if (!ctx->have_s4) {
     links_s4_kernel<<<cap_grid32((size_t)4 * ctx->g.V), 256, 0, s>>>(ctx->U32, l5, l3, ctx->g.V);
     ctx->have_s4 = true;
   }
+  return comp ? l3 : l5;
+}
+
+// out = H_W in on the S4 layout; comp selects the 3-float4 (compressed) links, 2 the
+// plane-staged kernel, 3 and 4 the 12-real kernel reading the centre first with 128 or
+// 256 threads per block.
+int launch_hw32_s4(ov_ctx* ctx, const float4* in, float4* out, int nrhs, int comp, cudaStream_t s) {
+  int st = OV_OK;
+  const float4* l5 = s4_links(ctx, false, s, &st);
+  const float4* l3 = s4_links(ctx, true, s, &st);
+  if (st != OV_OK) return st;
   const float diag = (float)(4.0 - ctx->m0);
   if (comp == 2) {  // one xy-plane per block, links and plane spinor staged in shared memory
     const int NTp = ctx->g.L[0] * ctx->g.L[1];
@@ -591,14 +624,18 @@ int launch_hw32_s4(ov_ctx* ctx, const float4* in, float4* out, int nrhs, int com
     OV_CHECK_LAUNCH(ctx, "hw32_plane_kernel");
     return OV_OK;
   }
-  constexpr int NT = 128;
+  const int NT = comp == 4 ? 256 : 128;
   dim3 grid((ctx->g.V + NT - 1) / NT, nrhs);
   cudaEvent_t ev;
   kt_begin(ctx, KC_DSLASH, s, &ev);
-  if (comp)
-    hw32_s4_kernel<true, NT><<<grid, NT, 0, s>>>(in, out, l3, ctx->g, diag);
+  if (comp == 4)
+    hw32_s4_kernel<true, 256, true><<<grid, NT, 0, s>>>(in, out, l3, ctx->g, diag);
+  else if (comp == 3)
+    hw32_s4_kernel<true, 128, true><<<grid, NT, 0, s>>>(in, out, l3, ctx->g, diag);
+  else if (comp)
+    hw32_s4_kernel<true, 128, false><<<grid, NT, 0, s>>>(in, out, l3, ctx->g, diag);
   else
-    hw32_s4_kernel<false, NT><<<grid, NT, 0, s>>>(in, out, l5, ctx->g, diag);
+    hw32_s4_kernel<false, 128, false><<<grid, NT, 0, s>>>(in, out, l5, ctx->g, diag);
   kt_end(ctx, KC_DSLASH, s, ev);
   OV_CHECK_LAUNCH(ctx, "hw32_s4_kernel");
   return OV_OK;

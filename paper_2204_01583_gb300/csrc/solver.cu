@@ -1393,38 +1393,49 @@ int solve_sign_soa(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc
   return solve_nodes_soa(ctx, b_soa, nsrc, ns, zh, ch, ctx->c0, out_soa, xs_soa, o, so, s);
 }
 
-// g = sum_j c_j (z_j - T_k)^-1 e_1 ||b|| per source (forward LDL^T sweep and back
-// substitution per node), from the recorded alpha (ha) and beta (hb), leading dimension ld.
+// FOM coefficients y = (z - T_k)^-1 e_1 ||b|| of one node from the recorded Lanczos
+// scalars al[0..k), be[0..k): forward LDL^T sweep (d_i, l_i = -beta_i / d_i, zeta_i =
+// omega_i / d_i) and back substitution y_i = zeta_i - l_i y_{i+1}.
+struct FomScratch {
+  std::vector<std::complex<double>> dd, ll, zt;
+};
+static void fom_coefficients(const double* al, const double* be, int k, double bnorm, std::complex<double> z,
+                             FomScratch& sc, std::vector<std::complex<double>>& yy) {
+  sc.dd.assign(k, 0.0);
+  sc.ll.assign(k, 0.0);
+  sc.zt.assign(k, 0.0);
+  yy.assign(k, 0.0);
+  if (k < 1) return;
+  std::complex<double> om = bnorm;
+  for (int i = 0; i < k; ++i) {
+    if (i == 0) {
+      sc.dd[0] = z - al[0];
+    } else {
+      sc.dd[i] = z - al[i] - be[i - 1] * be[i - 1] / sc.dd[i - 1];
+      om = -sc.ll[i - 1] * om;
+    }
+    sc.ll[i] = -be[i] / sc.dd[i];
+    sc.zt[i] = om / sc.dd[i];
+  }
+  yy[k - 1] = sc.zt[k - 1];
+  for (int i = k - 2; i >= 0; --i) yy[i] = sc.zt[i] - sc.ll[i] * yy[i + 1];
+}
+
+// g = sum_j c_j (z_j - T_k)^-1 e_1 ||b|| per source, from the recorded alpha (ha) and beta
+// (hb), leading dimension ld.
 static void lanczos_sum_coefficients(const ov_ctx* ctx, int nsrc, const std::vector<int>& kr,
                                      const std::vector<double>& bnorm, const std::vector<double>& ha,
                                      const std::vector<double>& hb, int ld, std::vector<double2>& g) {
   const int ns = (int)ctx->z.size();
   g.assign((size_t)nsrc * ld, make_double2(0.0, 0.0));
-  std::vector<std::complex<double>> dd, ll, zt, yy;
+  FomScratch sc;
+  std::vector<std::complex<double>> yy;
   for (int r = 0; r < nsrc; ++r) {
     const int k = kr[r];
     if (k < 1) continue;
-    const double* al = ha.data() + (size_t)r * ld;
-    const double* be = hb.data() + (size_t)r * ld;
-    dd.assign(k, 0.0);
-    ll.assign(k, 0.0);
-    zt.assign(k, 0.0);
-    yy.assign(k, 0.0);
     for (int j = 0; j < ns; ++j) {
       const std::complex<double> zj(ctx->z[j].x, ctx->z[j].y), cj(ctx->c[j].x, ctx->c[j].y);
-      std::complex<double> om = bnorm[r];
-      for (int i = 0; i < k; ++i) {
-        if (i == 0) {
-          dd[0] = zj - al[0];
-        } else {
-          dd[i] = zj - al[i] - be[i - 1] * be[i - 1] / dd[i - 1];
-          om = -ll[i - 1] * om;
-        }
-        ll[i] = -be[i] / dd[i];
-        zt[i] = om / dd[i];
-      }
-      yy[k - 1] = zt[k - 1];
-      for (int i = k - 2; i >= 0; --i) yy[i] = zt[i] - ll[i] * yy[i + 1];
+      fom_coefficients(ha.data() + (size_t)r * ld, hb.data() + (size_t)r * ld, k, bnorm[r], zj, sc, yy);
       for (int i = 0; i < k; ++i) {
         const std::complex<double> t = cj * yy[i];
         g[(size_t)r * ld + i].x += t.real();
@@ -1748,32 +1759,17 @@ static int nodes_coef(ov_ctx* ctx, const double2* b_soa, int nsrc, int ns, const
   std::vector<T> Yh((size_t)nsrc * ns * cap);
   std::vector<T> gh((size_t)nsrc * cap);
   std::vector<int> kr(nsrc);
-  std::vector<std::complex<double>> dd, ll, zt, yy, gs;
+  FomScratch sc;
+  std::vector<std::complex<double>> yy, gs;
   for (int r = 0; r < nsrc; ++r) {
     const int k = kr[r] = std::max(0, S[r].iter - 1);
     const double* al = ha.data() + (size_t)r * cap;
     const double* be = hb.data() + (size_t)r * cap;
-    dd.assign(k, 0.0);
-    ll.assign(k, 0.0);
-    zt.assign(k, 0.0);
-    yy.assign(k, 0.0);
     gs.assign(k, 0.0);
     for (int j = 0; j < ns && k > 0; ++j) {
       const std::complex<double> zj(zh[(size_t)r * ns + j].x, zh[(size_t)r * ns + j].y);
       const std::complex<double> cj(ch[(size_t)r * ns + j].x, ch[(size_t)r * ns + j].y);
-      std::complex<double> om = S[r].bnorm;
-      for (int i = 0; i < k; ++i) {
-        if (i == 0) {
-          dd[0] = zj - al[0];
-        } else {
-          dd[i] = zj - al[i] - be[i - 1] * be[i - 1] / dd[i - 1];
-          om = -ll[i - 1] * om;
-        }
-        ll[i] = -be[i] / dd[i];
-        zt[i] = om / dd[i];
-      }
-      yy[k - 1] = zt[k - 1];
-      for (int i = k - 2; i >= 0; --i) yy[i] = zt[i] - ll[i] * yy[i + 1];
+      fom_coefficients(al, be, k, S[r].bnorm, zj, sc, yy);
       for (int i = 0; i < k; ++i) {
         const double ni = (i == 0) ? S[r].bnorm : be[i - 1];
         const std::complex<double> y = yy[i] / ni;
