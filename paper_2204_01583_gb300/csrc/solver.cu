@@ -78,12 +78,19 @@ __device__ __forceinline__ void df_split(double x, float* d) {
   d[1] = __double2float_rn(x - (double)d[0]);
 }
 
-// inv_n, cm and their double-float forms from n_cur, n_prev and iter
+// inv_n, cm and (double-float vectors only) their double-float forms from n_cur, n_prev
+// and iter.  These run in one thread on the path between two launches, where every FP64
+// instruction waits for the previous one (GB300's FP64 rate is 1/64 of FP32): the
+// reciprocal is the correctly rounded one (the same value as 1.0 / n_cur), and the FP64
+// solve skips the splits it does not read.
+template <typename R>
 __device__ __forceinline__ void set_norm_scalars(SrcState* S) {
-  S->inv_n = 1.0 / S->n_cur;
+  S->inv_n = __drcp_rn(S->n_cur);
   S->cm = (S->iter > 1) ? S->n_cur / S->n_prev : 0.0;
-  df_split(S->inv_n, S->df + 0);
-  df_split(S->cm, S->df + 2);
+  if constexpr (std::is_same<R, DF>::value) {
+    df_split(S->inv_n, S->df + 0);
+    df_split(S->cm, S->df + 2);
+  }
 }
 
 // An FP64 recurrence scalar in the vector arithmetic type; for double-float, from its
@@ -370,7 +377,7 @@ __global__ void __launch_bounds__(NT1, k1_min_blocks<R>()) lanczos_hw_kernel(Sol
     a.cnt[2 * r] = 0;
     const double alpha = tot * inv_n;
     S->alpha = alpha;
-    df_split(alpha, S->df + 4);
+    if constexpr (std::is_same<R, DF>::value) df_split(alpha, S->df + 4);
     alpha_sh = alpha;
     if (a.hist_a) a.hist_a[(size_t)r * a.prm->max_iter + (i - 1)] = alpha;
     if (!isfinite(alpha)) {
@@ -405,7 +412,7 @@ __global__ void __launch_bounds__(NT1, k1_min_blocks<R>()) lanczos_hw_kernel(Sol
           d = make_double2(zj.x - alpha - b2 * ip.x, zj.y - b2 * ip.y);
           om = cmul(make_double2(-lprev.x, -lprev.y), q.omega);
         }
-        const double inv = 1.0 / (d.x * d.x + d.y * d.y);
+        const double inv = __drcp_rn(d.x * d.x + d.y * d.y);  // = 1.0 / |d|^2
         const double2 invd = make_double2(d.x * inv, -d.y * inv);
         zeta = cmul(om, invd);
         q.invd = invd;
@@ -438,7 +445,7 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
   using T = typename Store<R>::T;
   __shared__ double sh[NT2 / 32];
   __shared__ bool last;
-  __shared__ double beta_sh;
+  __shared__ double nrm2_sh;
   const int r = blockIdx.y;
   SrcState* S = a.src + r;
   if (S->done) return;
@@ -504,19 +511,23 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // ||u||^2 goes to every thread before the square root is taken: the node tests need
+  // only beta^2, and sqrt sits on one thread's serial FP64 path
   const double tot = sum_partials<NT2>(a.part2 + (size_t)r * gridDim.x, gridDim.x, sh);
   if (threadIdx.x == 0) {
     a.cnt[2 * r + 1] = 0;
-    beta_sh = sqrt(tot);
-    if (a.hist_b) a.hist_b[(size_t)r * a.prm->max_iter + (i - 1)] = beta_sh;
-    if (!isfinite(beta_sh)) mark_done(S, a.done_count, OV_ERR_BREAKDOWN);
+    nrm2_sh = tot;
+    if (!isfinite(tot)) {
+      if (a.hist_b) a.hist_b[(size_t)r * a.prm->max_iter + (i - 1)] = sqrt(tot);
+      mark_done(S, a.done_count, OV_ERR_BREAKDOWN);
+    }
   }
   __syncthreads();
-  const double beta = beta_sh;
-  if (!isfinite(beta)) return;
+  const double nrm2 = nrm2_sh;
+  if (!isfinite(nrm2)) return;
   const double tol = a.tol_src ? a.tol_src[r] : a.prm->tol;
   const double tol2 = tol * tol;
-  const double b2n = beta * beta * S->inv_b2;
+  const double b2n = nrm2 * S->inv_b2;
   int still = 0;
   for (int j0 = 0; j0 < ns; j0 += NT2) {
     const int j = j0 + threadIdx.x;
@@ -526,9 +537,9 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
       if (q.active) {
         q.res2 = b2n * (q.zeta.x * q.zeta.x + q.zeta.y * q.zeta.y);
         q.last_iter = i;
-        if (q.res2 <= tol2 || beta == 0.0) {
+        if (q.res2 <= tol2 || nrm2 == 0.0) {
           q.active = 0;
-          if (beta == 0.0) q.res2 = 0.0;
+          if (nrm2 == 0.0) q.res2 = 0.0;
         } else {
           act = true;
         }
@@ -537,10 +548,12 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
     still += __syncthreads_count(act);
   }
   if (threadIdx.x != 0) return;
+  const double beta = sqrt(nrm2);
+  if (a.hist_b) a.hist_b[(size_t)r * a.prm->max_iter + (i - 1)] = beta;
   S->n_prev = S->n_cur;
   S->n_cur = beta;
   S->iter = i + 1;
-  set_norm_scalars(S);
+  set_norm_scalars<R>(S);
   if (beta == 0.0) {
     mark_done(S, a.done_count, OV_OK);
   } else if (ns > 0 && still == 0) {
@@ -691,7 +704,7 @@ __global__ void __launch_bounds__(NT1, 4) lanczos_coop_kernel(SolveArgs<R> a, in
               S->iter = i;
               S->n_cur = s_ncur[r];
               S->n_prev = s_nprev[r];
-              set_norm_scalars(S);
+              set_norm_scalars<R>(S);
               S->status = (act > 0 && !beta0) ? OV_ERR_NOT_CONVERGED : OV_OK;
               S->done = 1;
             }
@@ -812,7 +825,7 @@ __global__ void regen_scalars_kernel(SolveArgs<R> a, RegenRec<R>* rec, int nsrc)
     const double n_i = (i == 1) ? S->bnorm : a.hist_b[(size_t)r * mi + i - 2];
     const double n_m = (i <= 2) ? S->bnorm : a.hist_b[(size_t)r * mi + i - 3];
     float d[6];
-    const double inv_n = 1.0 / n_i, cm = (i > 1) ? n_i / n_m : 0.0, alpha = a.hist_a[(size_t)r * mi + i - 1];
+    const double inv_n = __drcp_rn(n_i), cm = (i > 1) ? n_i / n_m : 0.0, alpha = a.hist_a[(size_t)r * mi + i - 1];
     df_split(inv_n, d + 0);
     df_split(cm, d + 2);
     df_split(alpha, d + 4);
@@ -925,7 +938,7 @@ __global__ void __launch_bounds__(NT2) lanczos_init_kernel(SolveArgs<R> a, const
   S->n_prev = 1.0;
   S->alpha = 0.0;
   S->iter = 1;
-  set_norm_scalars(S);
+  set_norm_scalars<R>(S);
   S->status = OV_OK;
   S->n_act = 0;
   S->node_updates = 0.0;
