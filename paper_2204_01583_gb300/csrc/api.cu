@@ -168,6 +168,7 @@ const double2* stage_in(ov_ctx* ctx, const void* p, size_t bytes, int host_io, c
 // Core of sgn / overlap: canonical b (device) -> S_N b (SoA, workspace).
 int sign_core(ov_ctx* ctx, const double2* b_dev, int nrhs, const ov_solve_opts& o, SolveOut* so, cudaStream_t s,
               double2** s_soa_out, double2* xs) {
+  NvtxRange nvtx_("sign_core");
   int st = OV_OK;
   const size_t n = (size_t)12 * ctx->g.V * nrhs;
   double2* b_soa = (double2*)ws_get(ctx, "api.b_soa", sizeof(double2) * n, &st);
@@ -268,6 +269,7 @@ int ov_destroy(ov_ctx* ctx) {
 const char* ov_last_error(const ov_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 int ov_set_gauge(ov_ctx* ctx, const double* U, int on_device, void* stream) {
+  NvtxRange nvtx_("ov_set_gauge");
   if (!ctx) return OV_ERR_INVALID_ARG;
   if (!U) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "null gauge pointer");
   DeviceGuard dg(ctx->device);
@@ -347,6 +349,7 @@ static int fp32_float4_launch(ov_ctx* ctx, int v, const float4* in, float4* out,
 }
 
 int ov_apply_HW(ov_ctx* ctx, const void* in, void* out, int nrhs, int precision, void* stream) {
+  NvtxRange nvtx_("ov_apply_HW");
   if (!ctx) return OV_ERR_INVALID_ARG;
   if (!ctx->have_gauge) return ctx_fail(ctx, OV_ERR_NO_GAUGE, "ov_set_gauge has not been called");
   if (nrhs < 0 || (nrhs > 0 && (!in || !out)) || in == out)
@@ -506,6 +509,7 @@ static int spectral_bounds(ov_ctx* ctx, int steps, cudaStream_t s, double* lo, d
 }
 
 int ov_place_contour(ov_ctx* ctx, int n_q, int steps, ov_spectrum* out, void* stream) {
+  NvtxRange nvtx_("ov_place_contour");
   if (!ctx) return OV_ERR_INVALID_ARG;
   if (!ctx->have_gauge) return ctx_fail(ctx, OV_ERR_NO_GAUGE, "ov_set_gauge has not been called");
   if (n_q < 2 || steps < 4) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "need n_q >= 2 and steps >= 4");
@@ -585,6 +589,7 @@ int ov_set_contour_zolotarev(ov_ctx* ctx, int n_poles, double lambda_min, double
 }
 
 int ov_place_zolotarev(ov_ctx* ctx, int n_poles, int steps, ov_spectrum* out, void* stream) {
+  NvtxRange nvtx_("ov_place_zolotarev");
   if (!ctx) return OV_ERR_INVALID_ARG;
   if (!ctx->have_gauge) return ctx_fail(ctx, OV_ERR_NO_GAUGE, "ov_set_gauge has not been called");
   if (n_poles < 1 || n_poles > 128 || steps < 4)
@@ -652,11 +657,13 @@ static int sign_or_overlap(ov_ctx* ctx, bool overlap, double m_q, const void* b,
 
 int ov_sgn_HW_apply(ov_ctx* ctx, const void* b, void* out, int nrhs, const ov_solve_opts* opts, ov_stats* stats,
                     void* stream) {
+  NvtxRange nvtx_("ov_sgn_HW_apply");
   return sign_or_overlap(ctx, false, 0.0, b, out, nrhs, opts, stats, stream);
 }
 
 int ov_overlap_apply(ov_ctx* ctx, double m_q, const void* b, void* out, int nrhs, const ov_solve_opts* opts,
                      ov_stats* stats, void* stream) {
+  NvtxRange nvtx_("ov_overlap_apply");
   return sign_or_overlap(ctx, true, m_q, b, out, nrhs, opts, stats, stream);
 }
 
@@ -684,6 +691,7 @@ __global__ void scale_kernel(double* __restrict__ p, double a, size_t n) {
 // force = fsc * dRe<eta_s, S_N b>/d omega.
 int vjp_core(ov_ctx* ctx, double a_eta, double gsc, double fsc, bool gamma5_eta, const void* eta, const void* b,
              void* grad_b, double* grad_links, const ov_solve_opts* opts, ov_stats* stats, void* stream) {
+  NvtxRange nvtx_("vjp_core");
   const double t0 = now_ms();
   if (!ctx) return OV_ERR_INVALID_ARG;
   if (!ctx->have_gauge) return ctx_fail(ctx, OV_ERR_NO_GAUGE, "ov_set_gauge has not been called");

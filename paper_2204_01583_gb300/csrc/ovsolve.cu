@@ -138,6 +138,7 @@ int dot(CgCtx& c, const double2* u, const double2* v, std::vector<double>& out) 
 
 extern "C" int ov_overlap_solve(ov_ctx* ctx, double m_q, const void* b, void* x, int nrhs, const ov_solve_opts* inner,
                                 double tol, int max_iter, ov_stats* stats, void* stream) {
+  NvtxRange nvtx_("ov_overlap_solve");
   const double t0 = now_ms();
   if (!ctx) return OV_ERR_INVALID_ARG;
   if (!ctx->have_gauge) return ctx_fail(ctx, OV_ERR_NO_GAUGE, "ov_set_gauge has not been called");

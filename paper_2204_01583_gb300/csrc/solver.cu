@@ -1180,6 +1180,7 @@ int launch_iteration(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, cudaStream_t s)
 template <typename R>
 int run_iterations(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, int nshift, int flavour, int max_iter,
                    const ov_solve_opts& o, cudaStream_t s, double* launches) {
+  NvtxRange nvtx_("lanczos iterations");
   const int chunk = o.check_every > 0 ? o.check_every : 32;
   const bool graph = o.use_graph && !ctx->timing;
   cudaGraphExec_t exec = nullptr;
@@ -1396,6 +1397,7 @@ int solve_nodes_soa_df(ov_ctx* ctx, const double2* b_soa, int nsrc, int ns, cons
 
 int solve_sign_soa(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc, const ov_solve_opts& o,
                    SolveOut* so, cudaStream_t s, double2* xs_soa) {
+  NvtxRange nvtx_("solve: vector-space form");
   const int ns = (int)ctx->z.size();
   std::vector<double2> zh((size_t)nsrc * ns), ch((size_t)nsrc * ns);
   for (int r = 0; r < nsrc; ++r)
@@ -1463,6 +1465,7 @@ static void lanczos_sum_coefficients(const ov_ctx* ctx, int nsrc, const std::vec
 template <typename R>
 static int solve_sign_stored(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc,
                              const ov_solve_opts& o, SolveOut* so, cudaStream_t s, int cap) {
+  NvtxRange nvtx_("solve: stored basis");
   const int ns = (int)ctx->z.size();
   const size_t n12 = (size_t)12 * ctx->g.V;
   SolveWs<R> w;
@@ -1564,6 +1567,7 @@ void merge_stats(SolveOut* tot, const SolveOut& b, bool first) {
 template <typename R>
 static int solve_sign_coef(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc, const ov_solve_opts& o,
                            SolveOut* so, cudaStream_t s) {
+  NvtxRange nvtx_("solve: coefficient space");
   if (o.mode == OV_MODE_FP64_REGEN) return solve_sign_regen<R>(ctx, b_soa, out_soa, nsrc, o, so, s);
   size_t freeb = 0, totalb = 0;
   cudaMemGetInfo(&freeb, &totalb);
@@ -1851,6 +1855,7 @@ int solve_sign_2pass(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int ns
 //  Finally the FP64 weighted sum s = c0 b + sum_j c_j y_j.
 int solve_sign_mixed(ov_ctx* ctx, const double2* b_soa, double2* out_soa, int nsrc, const ov_solve_opts& o,
                      SolveOut* so, cudaStream_t s) {
+  NvtxRange nvtx_("solve: mixed precision");
   const int nq = (int)ctx->z.size();
   const size_t n12 = (size_t)12 * ctx->g.V;
   const int nrhs = nsrc * nq;
