@@ -426,7 +426,10 @@ def run_ours(args, wl):
 #   lanczos_regen_kernel:  stencil + Lanczos update + s += g v (1368 + 12 x 24 flop;
 #                          576 + 4 x 192 B + sum read+write 384 B)            per si
 #   lanczos_coop_kernel:   the two above for every iteration in one persistent launch  per si
+#   basis_sum_kernel:      s += g_i v_i over the stored basis, one basis vector per
+#                          source-iteration (12 x 8 flop; the vector read, 192 B)  per si
 FP64_WORK = {
+    "basis_sum_kernel": {"si": (96.0, 192.0)},
     "lanczos_coop_kernel": {"si": (1560.0, 1728.0)},
     "lanczos_hw_kernel": {"si": (1440.0, 1152.0)},
     "lanczos_update_kernel": {"si": (120.0, 576.0), "nu": (192.0, 384.0)},

@@ -11,7 +11,8 @@
 
 const char* const kKernelClassNames[KC_COUNT] = {"hw_kernel",         "lanczos_hw_kernel", "lanczos_update_kernel",
                                                   "layout_kernels",    "init_kernels",      "force_kernel",
-                                                  "residual_kernels",  "lanczos_regen_kernel", "lanczos_coop_kernel"};
+                                                  "residual_kernels",  "lanczos_regen_kernel", "lanczos_coop_kernel",
+                                                  "basis_sum_kernel"};
 
 // ------------------------------------------------------------ utilities
 

@@ -59,8 +59,9 @@ enum KernelClass {
   KC_MISC,           // initialisation and small kernels
   KC_FORCE,          // link force
   KC_RESIDUAL,       // FP64 true residuals (mixed mode)
-  KC_REGEN,          // second pass of the two-pass mode
+  KC_REGEN,          // regeneration pass of the two-pass mode
   KC_COOP,           // persistent cooperative Lanczos loop
+  KC_BASIS_SUM,      // s = c0 b + sum_i g_i v_i from a stored basis
   KC_COUNT
 };
 

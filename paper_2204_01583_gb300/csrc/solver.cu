@@ -1519,10 +1519,10 @@ static int solve_sign_stored(ov_ctx* ctx, const double2* b_soa, double2* out_soa
   if (e == cudaSuccess) e = cudaMemcpyAsync(krd, kr.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy coefficients");
   cudaEvent_t ev;
-  kt_begin(ctx, KC_REGEN, s, &ev);
+  kt_begin(ctx, KC_BASIS_SUM, s, &ev);
   basis_sum_kernel<R><<<dim3((unsigned)((n12 + 255) / 256), nsrc), 256, 0, s>>>(w.a.ring, cap + 3, gd, cap, krd,
                                                                              w.a.sacc, n12);
-  kt_end(ctx, KC_REGEN, s, ev);
+  kt_end(ctx, KC_BASIS_SUM, s, ev);
   OV_CHECK_LAUNCH(ctx, "basis_sum_kernel");
   so->launches = launches + 3.0;
   e = cudaMemcpyAsync(out_soa, w.a.sacc, sizeof(double2) * n12 * nsrc, cudaMemcpyDeviceToDevice, s);
@@ -1805,8 +1805,11 @@ static int nodes_coef(ov_ctx* ctx, const double2* b_soa, int nsrc, int ns, const
   if (e == cudaSuccess) e = cudaMemcpyAsync(krd, kr.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(sums, 0, sizeof(double2) * n12 * nsrc, s);
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy node coefficients");
+  cudaEvent_t ev;
+  kt_begin(ctx, KC_BASIS_SUM, s, &ev);
   basis_sum_kernel<R><<<dim3((unsigned)((n12 + 255) / 256), nsrc), 256, 0, s>>>(w.a.ring, cap + 3, gd, cap, krd,
                                                                              sums, n12);
+  kt_end(ctx, KC_BASIS_SUM, s, ev);
   OV_CHECK_LAUNCH(ctx, "basis_sum_kernel");
   constexpr int JT = 8;
   for (int j0 = 0; j0 < ns; j0 += chunk) {
