@@ -224,8 +224,8 @@ int ov_overlap_vjp(ov_ctx* ctx, double m_q, const void* eta, const void* b, void
  * D^dag D x = D^dag b with D^dag = gamma5 D gamma5 (exact for the hermitian S_N).  Every
  * CG iteration applies D twice (each a full shifted solve with the options in `inner`;
  * NULL = defaults).  The products of iteration k are solved to the inner tolerance
- * inner->tol times max(1, ||r_0|| / (64 ||r_k||)) for the least converged source, at most
- * max(inner->tol, 1e-6): an error in a product matters in proportion to the current
+ * inner->tol times max(1, ||r_0|| / (4 ||r_k||)) for the least converged source, at most
+ * max(inner->tol, 1e-4): an error in a product matters in proportion to the current
  * residual, so later products need less accuracy (relaxed inexact Krylov); the true
  * residual below is checked with a product at inner->tol.  b, x: canonical complex128 spinors [nrhs][t][z][y][x][4][3], device
  * pointers (host pointers when inner->host_io), b != x; the caller owns both.  Stops a
