@@ -59,7 +59,7 @@ WORKLOADS = {
     # stencil only: H_W on 12 right-hand sides (diagnostic of the HBM roofline)
     "dslash-16^3x32-fp32-12rhs": dict(dims=(16, 16, 16, 32), eps=0.6, nsrc=12, kind="dslash", prec="fp32"),
     "dslash-16^3x32-fp64-12rhs": dict(dims=(16, 16, 16, 32), eps=0.6, nsrc=12, kind="dslash", prec="fp64"),
-    # sigma vs nodes per contour with the paper's two-ellipse contour (rescaled), 8^4
+    "dslash-16^4-fp32-12rhs": dict(dims=(16, 16, 16, 16), eps=0.5, nsrc=12, kind="dslash", prec="fp32"),
     # overlap solve x = D_ov^-1 b (CG on the normal equations, double-float inner solves)
     "ovsolve-8^4-mq0.05-4src": dict(dims=(8, 8, 8, 8), eps=0.5, m_q=0.05, n_q=64, nsrc=4, src="gauss", tol=1e-10,
                                     inner_tol=1e-12, mode="f32x2", kind="ovsolve"),
@@ -69,6 +69,7 @@ WORKLOADS = {
     # the same measure with Zolotarev's optimal node set (n pole pairs = 2n nodes) from Lanczos bounds
     "sigma-8^4-zolotarev": dict(dims=(8, 8, 8, 8), eps=0.5, nsrc=4, src="gauss", kind="sigma", rule="zolotarev",
                                 n_list=(4, 8, 12, 16, 20)),
+    # sigma vs nodes per contour with the paper's two-ellipse contour (rescaled), 8^4
     "sigma-8^4-paper-contour": dict(dims=(8, 8, 8, 8), eps=0.5, nsrc=4, src="gauss", kind="sigma",
                                     n_list=(100, 250, 500, 1000)),
 }
