@@ -183,3 +183,41 @@ int oracle_sign_apply(const double* U, const double* bd, const int* dims, double
   if (!ys) free(Y);
   return bad;
 }
+
+/*
+ * The same quadrature sum for several sources at once: out_r = c0 b_r + sum_j c_j y_{r,j}
+ * with one CGNR per (source, node) pair, OpenMP over all pairs (so that a few nodes of
+ * many sources fill the cores).  b and out hold nsrc canonical spinors back to back;
+ * iters and relres receive nsrc * n_nodes entries, source-major.  Returns 0 if every
+ * solve converged.
+ */
+int oracle_sign_apply_many(const double* U, const double* bd, const int* dims, double m0, double r,
+                           int bc_t, int nsrc, int n_nodes, const double* z, const double* c,
+                           double c0re, double c0im, double tol, int maxiter, double* outd,
+                           int* iters, double* relres) {
+  long n = 12L * dims[0] * dims[1] * dims[2] * dims[3];
+  long npair = (long)nsrc * n_nodes;
+  cplx* Y = malloc(sizeof(cplx) * n * (npair > 0 ? npair : 1));
+  if (!Y) return -1;
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+  for (long q = 0; q < npair; ++q) {
+    long rr = q / n_nodes, j = q % n_nodes;
+    int rc = oracle_cgnr(U, bd + 2 * rr * n, dims, m0, r, bc_t, z[2 * j], z[2 * j + 1], tol, maxiter,
+                         (double*)(Y + q * n), &iters[q], &relres[q]);
+    if (rc) bad = 1;
+  }
+  cplx c0 = c0re + I1 * c0im;
+  for (long rr = 0; rr < nsrc; ++rr) {
+    const cplx* b = (const cplx*)bd + rr * n;
+    cplx* out = (cplx*)outd + rr * n;
+    for (long i = 0; i < n; ++i) out[i] = c0 * b[i];
+    for (int j = 0; j < n_nodes; ++j) {
+      cplx cj = c[2 * j] + I1 * c[2 * j + 1];
+      const cplx* yj = Y + (rr * n_nodes + j) * n;
+      for (long i = 0; i < n; ++i) out[i] += cj * yj[i];
+    }
+  }
+  free(Y);
+  return bad;
+}

@@ -115,3 +115,65 @@ def test_zolotarev_beats_trapezoid_on_spectrum():
     ze, ce, c0e = contour.single_contour(64, 0.525 * b, 0.525 * b, 0.3)
     err_e = np.abs(contour.rational(lam, ze, ce, c0e).real - np.sign(lam)).max()
     assert err < 1e-3 * err_e
+
+
+# ------------------------------------- single-contour rule vs the spectral sign (Eq. 2)
+
+def _single_contour_error(rule, n):
+    """Element-wise error of the sign operator that a single-contour coefficient rule gives,
+    S_N b = c0 b + sum_j c_j (z_j - H)^-1 b with one dense LU solve per node (Eqs. 5-7),
+    against the spectral sign of Eq. 2, V sgn(Lambda) V^dag b (LAPACK zheevd), on a
+    2x2x2x4 lattice (H_W of Eq. 1, |lambda| in [0.25, 5.9]).  The ellipse runs from 0 to
+    6.8 and so encloses exactly the positive spectrum."""
+    import synthetic as S
+    from oracle import sign, wilson
+
+    U = S.su3_links((2, 2, 2, 4), 0.5, 101)
+    H = wilson.dense_HW(U, 1.6)
+    b = S.gaussian_spinor((2, 2, 2, 4), 102).reshape(-1)
+    lam, V = np.linalg.eigh(H)
+    exact = V @ (np.sign(lam) * (V.conj().T @ b))
+    z, c, c0 = rule(n, 3.4, 3.4, 0.3)
+    s = sign.sign_apply_dense(H, b, z, c, c0)
+    return np.abs(s - exact).max() / np.abs(exact).max()
+
+
+def test_single_contour_pinned_to_spectral_sign():
+    """sgn = 2 P_Gamma - 1 (Eq. 3 and the remark after it, P_+ + P_- = 1 without zero modes):
+    the rule reaches the exact sign function of Eq. 2 within the trapezoid error, which
+    falls geometrically with N (64 nodes: ~5e-7 at this gap; 192 nodes: rounding)."""
+    assert _single_contour_error(contour.single_contour, 64) < 1e-5
+    assert _single_contour_error(contour.single_contour, 192) < 1e-11
+
+
+def _mutants():
+    """Plausible slips in the single-contour rule, planted in copies of the oracle's."""
+    def c0_sign(n, g, r, a):
+        z, c, c0 = contour.single_contour(n, g, r, a)
+        return z, c, -c0
+
+    def no_factor_two(n, g, r, a):
+        z, c, c0 = contour.single_contour(n, g, r, a)
+        return z, c / 2, c0
+
+    def conj_weights(n, g, r, a):
+        z, c, c0 = contour.single_contour(n, g, r, a)
+        return z, c.conj(), c0
+
+    def neg_weights(n, g, r, a):
+        z, c, c0 = contour.single_contour(n, g, r, a)
+        return z, -c, c0
+
+    def alpha_on_wrong_part_of_w(n, g, r, a):
+        th = 2.0 * np.pi * (np.arange(1, n + 1) - 0.5) / n
+        z = g + r * (np.cos(th) + 1j * a * np.sin(th))
+        w = np.cos(th) + 1j * a * np.sin(th)
+        return z, 2.0 * r * w / n, -1.0 + 0.0j
+
+    return [c0_sign, no_factor_two, conj_weights, neg_weights, alpha_on_wrong_part_of_w]
+
+
+@pytest.mark.parametrize("mutant", _mutants(), ids=lambda f: f.__name__)
+def test_single_contour_pin_rejects_planted_mistakes(mutant):
+    """Each planted slip moves the operator away from sgn(H) by O(1): the pin above fails it."""
+    assert _single_contour_error(mutant, 64) > 1e-2
