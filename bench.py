@@ -7,19 +7,23 @@
 A step is one pass of the hot path over one batch of synthetic sources:
 D_ov(m_q) b = (1+m_q)/2 b + (1-m_q)/2 gamma5 S_N b for every source of the batch,
 S_N b = c0 b + sum_j c_j (z_j - H_W)^-1 b from one shifted Krylov solve (Eqs. 1, 5-7).
-The contour is placed once per gauge field from Lanczos bounds (setup, untimed).
-The metric is source applies per second.  Prints ONE JSON line on rank 0.
+The default workload is 16^3 x 32 (eps 0.6, m_q 0.01), N_q = 64, the 12 spin-colour point
+sources, in the FP64 coefficient-space form; the contour is one explicit ellipse shared
+with the reference arm.  The metric is source applies per second.  The same line carries
+the double-float and FP32-refinement forms on the same step (speed-up and difference),
+the FP32 stencil's HBM bandwidth on 12 right-hand sides, the dominant kernel's roofline
+and the CPU oracle's throughput.  Prints ONE JSON line on rank 0.
 
 Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on
 the launching stream; a 256 MiB buffer is written between timed steps to flush
 L2; barrier + synchronize on both sides; max over ranks.  The end-to-end figure
 repeats the K steps through the same C-ABI call with pinned HOST buffers (copies
 inside the timed region).  Kernel durations for the roofline come from the
-library's per-launch CUDA events on the same stream (a separate K-step pass,
+library's per-launch CUDA events on the same stream (a separate pass of a few steps,
 because the timed pass replays CUDA graphs that cannot hold those events).
 
---impl reference times the FP64 CPU oracle (per-node CGNR solves and the
-weighted sum) on the host cores, on a bounded sample of the same workload.
+--impl reference times the FP64 CPU oracle (per-node CGNR solves and the weighted
+sum) on the host cores, on bounded slices of the same workload (see OracleSample).
 """
 from __future__ import annotations
 
@@ -46,16 +50,23 @@ UNIT = "applies/s"
 FP64_PEAK_TFLOPS = 1.25
 HBM_FALLBACK_GBS = 6800.0
 
+# The contour of the sign workloads: one explicit single ellipse, the same for both arms
+# (recorded in the line's config).  ||H_W|| <= |4 - m0| + 4 = 6.4 for every SU(3) field at
+# r = 1 (each of the eight hops has norm 1/2), so the ellipse from 0 to 1.05 x 6.4 encloses
+# the whole positive spectrum; alpha = 0.25 minimises max |r_N - sgn| over +-[0.3, 6.4] at
+# 64 nodes (4.4e-7).  The library's Lanczos placement runs too, untimed, for the spectrum.
+ELLIPSE = dict(gamma=3.36, rho=3.36, alpha=0.25)
+
 WORKLOADS = {
     # name: lattice, link roughness, quark mass, nodes, sources, source kind, tolerance, solver mode
-    "8^4-fp64-nq64-4src": dict(dims=(8, 8, 8, 8), eps=0.5, m_q=0.05, n_q=64, nsrc=4, src="gauss", tol=1e-12,
-                               mode="fp64_2pass"),
-    "4^4-fp64-nq32-1src": dict(dims=(4, 4, 4, 4), eps=0.3, m_q=0.1, n_q=32, nsrc=1, src="gauss", tol=1e-12,
-                               mode="fp64"),
-    "16^4-nq64-12pt": dict(dims=(16, 16, 16, 16), eps=0.5, m_q=0.05, n_q=64, nsrc=12, src="point", tol=1e-12,
-                           mode="f32x2"),
     "16^3x32-nq64-12pt": dict(dims=(16, 16, 16, 32), eps=0.6, m_q=0.01, n_q=64, nsrc=12, src="point", tol=1e-12,
-                              mode="f32x2"),
+                              mode="fp64_2pass", compare=("f32x2", "mixed"), dslash=True, ellipse=ELLIPSE),
+    "16^4-nq64-12pt": dict(dims=(16, 16, 16, 16), eps=0.5, m_q=0.05, n_q=64, nsrc=12, src="point", tol=1e-12,
+                           mode="fp64_2pass", compare=("f32x2",), dslash=True, ellipse=ELLIPSE),
+    "8^4-fp64-nq64-4src": dict(dims=(8, 8, 8, 8), eps=0.5, m_q=0.05, n_q=64, nsrc=4, src="gauss", tol=1e-12,
+                               mode="fp64_2pass", compare=("f32x2",), ellipse=ELLIPSE),
+    "4^4-fp64-nq32-1src": dict(dims=(4, 4, 4, 4), eps=0.3, m_q=0.1, n_q=32, nsrc=1, src="gauss", tol=1e-12,
+                               mode="fp64", ellipse=ELLIPSE),
     # stencil only: H_W on 12 right-hand sides (diagnostic of the HBM roofline)
     "dslash-16^3x32-fp32-12rhs": dict(dims=(16, 16, 16, 32), eps=0.6, nsrc=12, kind="dslash", prec="fp32"),
     "dslash-16^3x32-fp64-12rhs": dict(dims=(16, 16, 16, 32), eps=0.6, nsrc=12, kind="dslash", prec="fp64"),
@@ -73,10 +84,12 @@ WORKLOADS = {
     "sigma-8^4-paper-contour": dict(dims=(8, 8, 8, 8), eps=0.5, nsrc=4, src="gauss", kind="sigma",
                                     n_list=(100, 250, 500, 1000)),
 }
-DEFAULT_WORKLOAD = "8^4-fp64-nq64-4src"
+DEFAULT_WORKLOAD = "16^3x32-nq64-12pt"
 # arithmetic type of the vector work per solver mode (scalars, inner products and the sum stay f64)
 DTYPES = {"fp64": "f64", "fp64_2pass": "f64", "fp64_regen": "f64", "mixed": "f32+f64", "f32x2": "f32x2"}
 M0 = 1.6
+# the oracle's resolvent tolerance (per-node CGNR, true relative residual)
+ORACLE_TOL = 1e-13
 
 
 def parse():
@@ -91,7 +104,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variant", type=int, default=None, help="dslash workloads: time only this FP32 stencil variant")
     ap.add_argument("--compare-steps", type=int, default=2,
-                    help="mixed workloads: steps of each plain FP64 form timed for the comparison")
+                    help="steps of each comparison mode (the workload's 'compare' list) timed beside the line")
+    ap.add_argument("--no-dslash", action="store_true", help="skip the FP32 stencil measurement")
+    ap.add_argument("--parallel", default="sources", choices=["sources", "nodes"],
+                    help="N > 1: independent sources per GPU (weak), or the contour nodes split over the GPUs "
+                         "with one sum-allreduce per step (strong)")
     ap.add_argument("--nsrc", type=int, default=None, help="use only the first N sources (profiling cases)")
     ap.add_argument("--max-iter", type=int, default=None,
                     help="cap the Krylov iterations (profiling cases; the line is then not a valid measurement)")
@@ -174,54 +191,127 @@ class ClockSampler:
 
 # ------------------------------------------------------------- oracle (CPU)
 
-def oracle_sample(U, b0, z, c, c0, stride):
-    """Time the FP64 CPU oracle on every `stride`-th node of one source; returns
-    (seconds, nodes timed, threads)."""
+def workload_contour(wl):
+    """(gamma, rho, alpha) of the workload's explicit single ellipse (both arms)."""
+    e = wl["ellipse"]
+    return e["gamma"], e["rho"], e["alpha"]
+
+
+def oracle_threads():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+class OracleSample:
+    """Bounded timing of the FP64 CPU oracle (per-node CGNR to 1e-13 on (z_j - H_W) y = b,
+    Eq. 6, then the weighted sum of Eqs. 5-7) on one source of the workload.
+
+    One apply solves every node to 1e-13, which at 16^3 x 32 takes hours on the host.  The
+    sample runs every `stride`-th node (as many as the host has cores, at most 16) for a
+    capped number of CGNR iterations, in parallel over nodes.  From the true residual each
+    node reaches, its iterations to 1e-13 are extrapolated geometrically (a node that
+    converged inside the sample counts its own iterations); the sampled nodes stand for
+    all of them.  CG slows down as it meets the small eigenvalues of the normal
+    equations, so the extrapolated count is low and the estimate favours the oracle.
+    Work of one apply = node-iterations; throughput = node-iterations per second of
+    the sample."""
+
+    def __init__(self, U, b0, z, c, c0, k_iter):
+        from oracle import cimpl
+
+        cimpl.build()
+        n = len(z)
+        self.threads = oracle_threads()
+        nsamp = max(1, min(16, self.threads, n))
+        self.stride = max(1, n // nsamp)
+        self.idx = np.arange(0, n, self.stride)[:nsamp]
+        self.U, self.b0, self.z, self.c, self.c0, self.n = U, b0, z, c, c0, n
+        dt, iters, res = self.run(k_iter)
+        need = []
+        for it, r in zip(iters, res):
+            if it < k_iter or r <= ORACLE_TOL:
+                need.append(float(it))
+            else:
+                need.append(it * np.log(ORACLE_TOL) / np.log(max(min(r, 0.999999), 1e-300)))
+        self.k_iter = k_iter
+        self.work = float(np.sum(need)) * n / len(self.idx)  # node-iterations of one apply
+        self.rate = float(np.sum(iters)) / dt                 # node-iterations per second
+        self.setup_s = dt
+        self.need = need
+
+    def run(self, k_iter):
+        from oracle import cimpl
+
+        t0 = time.perf_counter()
+        _, iters, res = cimpl.sign_apply(self.U, self.b0, self.z[self.idx], self.c[self.idx], 0.0, M0,
+                                         tol=ORACLE_TOL, maxiter=int(k_iter), strict=False)
+        return time.perf_counter() - t0, iters, res
+
+    def applies_per_s(self):
+        return self.rate / self.work
+
+    def describe(self):
+        return {
+            "cores": int(min(self.threads, len(self.idx))), "host_cpu_count": os.cpu_count(),
+            "sampled_nodes": int(len(self.idx)), "nodes": int(self.n),
+            "cgnr_iterations_sampled": int(self.k_iter),
+            "extrapolated_iterations_per_node": [int(round(x)) for x in self.need],
+            "sample": (f"source 0, {len(self.idx)} of {self.n} nodes (every {self.stride}th), per-node CGNR "
+                       f"(oracle, FP64) capped at {self.k_iter} iterations in parallel over nodes; iterations "
+                       f"to {ORACLE_TOL:g} extrapolated per node from its residual reduction (geometric; "
+                       f"favours the oracle), scaled to all {self.n} nodes: EXTRAPOLATED, not a full apply"),
+        }
+
+
+def oracle_iteration_seconds(U, b0):
+    """Seconds of one CGNR iteration of the C oracle (two H_W applies and the vector
+    updates), from one timed H_W apply; sizes the bounded samples."""
     from oracle import cimpl
 
     cimpl.build()
-    idx = np.arange(0, len(z), stride)
+    cimpl.hw_apply(U, b0, M0)
     t0 = time.perf_counter()
-    cimpl.sign_apply(U, b0, z[idx], c[idx], 0.0, M0, tol=1e-13)
-    dt = time.perf_counter() - t0
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return dt, len(idx), min(threads, len(idx))  # OpenMP runs over nodes
-
-
-def reference_contour(wl):
-    """The contour the GPU arm places, restated on the host for the oracle: a single
-    ellipse from 0 to 1.05 x the spectral bound.  The bound comes from the free-field
-    formula scaled by the link roughness headroom (no GPU on this arm)."""
-    from oracle import contour, freefield
-
-    lo, hi = freefield.spectrum_bounds(tuple(reversed(wl["dims"])), M0)
-    R = 1.05 * hi * 1.05
-    return contour.single_contour(wl["n_q"], R / 2, R / 2, 0.25)
+    cimpl.hw_apply(U, b0, M0)
+    return 2.3 * (time.perf_counter() - t0)
 
 
 def run_reference(args, wl):
+    """The oracle as it stands, timed on the host cores on the workload's explicit contour
+    (the same nodes as the GPU arm), each step a bounded slice of one apply: every sampled
+    node advances `k_step` CGNR iterations.  The fraction of one apply a step covers comes
+    from the untimed setup sample (OracleSample), so value = fraction / step time."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
+    from oracle import contour
+
     U, b = workload_inputs(wl, 0)
-    z, c, c0 = reference_contour(wl)
-    stride = max(1, wl["n_q"] // 16)  # 16 nodes per step: a bounded sample
+    g, r, a = workload_contour(wl)
+    z, c, c0 = contour.single_contour(wl["n_q"], g, r, a)
+    t_it = oracle_iteration_seconds(U, b[0])
+    k_setup = int(np.clip(15.0 / t_it, 10, 4000))
+    k_step = int(np.clip(3.0 / t_it, 2, 1000))
+    samp = OracleSample(U, b[0], z, c, c0, k_setup)
     for _ in range(args.warmup):
-        oracle_sample(U, b[0], z, c, c0, stride)
-    times = []
+        samp.run(k_step)
+    times, iters_done = [], 0
     for _ in range(args.steps):
-        dt, nn, threads = oracle_sample(U, b[0], z, c, c0, stride)
-        times.append(dt * len(z) / nn)  # seconds per source apply, scaled to all nodes
-    per_apply = statistics.mean(times)
-    value = 1.0 / per_apply
+        dt, iters, _ = samp.run(k_step)
+        times.append(dt)
+        iters_done += int(np.sum(iters))
+    total = sum(times)
+    applies = iters_done / samp.work  # fraction of one source apply covered by the timed steps
+    value = applies / total
+    cb = samp.describe()
+    cb.update({"value": value, "unit": UNIT, "kind": "oracle",
+               "timed_steps": f"{args.steps} steps, each every sampled node advancing {k_step} CGNR iterations "
+                              f"({applies / args.steps:.3g} of one source apply per step)"})
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_apply * 1e3 * wl["nsrc"],
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+        "applies_per_step": applies / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_dict(args, wl, "fp64"),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"per step: source 0, {nn} of {len(z)} nodes (every {stride}th), per-node CGNR "
-                                   f"to 1e-13 and weighted sum; time scaled by {len(z)}/{nn}"},
+        "config": config_dict(args, wl, "oracle: per-node CGNR, FP64"),
+        "cpu_baseline": cb,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -229,14 +319,21 @@ def run_reference(args, wl):
 
 
 def config_dict(args, wl, mode):
+    g, r, a = workload_contour(wl)
     c = {
         "workload": args.workload, "lattice": "x".join(map(str, wl["dims"])), "link_eps": wl["eps"], "m0": M0,
         "r": 1.0, "bc_t": "antiperiodic", "m_q": wl["m_q"], "N_q": wl["n_q"],
         "sources_per_gpu": args.nsrc or wl["nsrc"],
-        "source": "complex Gaussian" if wl["src"] == "gauss" else "spin-colour point sources",
-        "tol": wl["tol"], "mode": mode, "contour": "single ellipse placed from Lanczos bounds (setup, untimed)",
-        "l2": "256 MiB buffer written between timed steps", "parallelism": f"independent sources per GPU x{args.gpus}",
-        "graph_branches": args.concurrency or "auto",
+        "source": "complex Gaussian" if wl["src"] == "gauss" else "12 spin-colour point sources at the origin",
+        "tol": wl["tol"], "mode": mode,
+        "contour": {"form": "single ellipse (sgn = 2 P - 1), trapezoid rule of Eq. 7", "n_q": wl["n_q"],
+                    "gamma": g, "rho": r, "alpha": a,
+                    "why": "explicit and shared by both arms; encloses (0, 6.72], and |lambda| <= 6.4 for any "
+                           "SU(3) field at m0 = 1.6"},
+        "l2": "256 MiB buffer written between timed steps", "graph_branches": args.concurrency or "auto",
+        "parallelism": (f"contour nodes split over {args.gpus} GPUs, one sum-allreduce per step"
+                        if getattr(args, "parallel", "sources") == "nodes"
+                        else f"independent sources per GPU x{args.gpus}"),
     }
     if args.max_iter is not None:
         c["profiling_case"] = f"Krylov iterations capped at {args.max_iter}: not a measurement of the workload"
@@ -279,6 +376,23 @@ def hbm_peak():
         return HBM_FALLBACK_GBS, "fallback"
 
 
+def timed_steps(step, steps, stream, flush):
+    """Device time (ms) of each step: CUDA events on the launching stream, L2 flushed first."""
+    import torch
+
+    ts, out = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out.append(step())
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return ts, out
+
+
 def run_ours(args, wl):
     import torch
 
@@ -291,27 +405,40 @@ def run_ours(args, wl):
     from paper_2204_01583_gb300 import build as build_lib
 
     build_lib()
-    from paper_2204_01583_gb300 import lib
+    from paper_2204_01583_gb300 import lib, parallel
 
     mode = args.mode or wl["mode"]
-    U, b = workload_inputs(wl, rank)
+    nodes_split = args.parallel == "nodes"
+    U, b = workload_inputs(wl, 0 if nodes_split else rank)
     if args.nsrc:
         b = b[: args.nsrc]
     nsrc = b.shape[0]
     dev = torch.device("cuda", local)
     ctx = lib.Context(wl["dims"], bc_t=-1, m0=M0, device=local)
     ctx.set_gauge(torch.from_numpy(U).to(dev))
-    spec = ctx.place_contour(wl["n_q"], steps=150)
+    spec = ctx.place_contour(wl["n_q"], steps=150)  # spectrum report (untimed); the solve uses the explicit ellipse
+    g, r, a = workload_contour(wl)
+    ctx.set_contour_ellipse(wl["n_q"], g, r, a)
+    if nodes_split:
+        z, c, c0 = ctx.get_contour()
+        zr, cr, c0r = parallel.node_shard(z, c, c0, rank, world)
+        ctx.set_contour(zr, cr, c0r)
     bd = torch.from_numpy(b).to(dev)
     out = torch.empty_like(bd)
     capped = args.max_iter is not None
-    opts = ctx.opts(mode=mode, tol=wl["tol"], max_iter=args.max_iter or 20000)
+    max_iter = args.max_iter or 20000
+    opts = ctx.opts(mode=mode, tol=wl["tol"], max_iter=max_iter)
     ctx.set_concurrency(args.concurrency)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step(o=opts, src=bd, dst=out):
-        return ctx.overlap(wl["m_q"], src, dst, nsrc, o, allow_not_converged=capped)
+    def step(o=opts, src=bd, dst=out, s=None):
+        if nodes_split:  # partial sum over this rank's nodes, then the sum over ranks
+            st = ctx.sgn(src, dst, nsrc, o, stream=s, allow_not_converged=capped)
+            if world > 1:
+                parallel.allreduce_sum(dst)
+            return st
+        return ctx.overlap(wl["m_q"], src, dst, nsrc, o, stream=s, allow_not_converged=capped)
 
     def barrier():
         if world > 1:
@@ -320,66 +447,45 @@ def run_ours(args, wl):
             dist.barrier()
         torch.cuda.synchronize()
 
+    def max_over_ranks(x):
+        if world > 1:
+            import torch.distributed as dist
+
+            t = torch.tensor([x], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return x
+
     for _ in range(args.warmup):
         step()
     barrier()
     sampler = ClockSampler(local)
     sampler.start()
-    t_steps, stats = [], []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        stats.append(step())
-        e1.record(stream)
-        e1.synchronize()
-        t_steps.append(e0.elapsed_time(e1))
+    t_steps, stats = timed_steps(step, args.steps, stream, flush)
     barrier()
     clocks = sampler.stop()
-    total_ms = sum(t_steps)
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    applies = nsrc * args.steps * world
+    total_ms = max_over_ranks(sum(t_steps))
+    applies = nsrc * args.steps * (1 if nodes_split else world)
     value = applies / (total_ms / 1e3)
 
     # end to end: the same call with pinned host buffers, copies inside the timed region
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not nodes_split:
         hb = torch.from_numpy(b).pin_memory()
         ho = torch.empty_like(hb).pin_memory()
-        ho_opts = ctx.opts(mode=mode, tol=wl["tol"], host_io=True, max_iter=args.max_iter or 20000)
-        step(ho_opts, hb, ho)
+        ho_opts = ctx.opts(mode=mode, tol=wl["tol"], host_io=True, max_iter=max_iter)
+        step(ho_opts, hb, ho, stream)
         barrier()
-        te = []
-        for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ctx.overlap(wl["m_q"], hb, ho, nsrc, ho_opts, stream=stream, allow_not_converged=capped)
-            e1.record(stream)
-            e1.synchronize()
-            te.append(e0.elapsed_time(e1))
+        te, _ = timed_steps(lambda: step(ho_opts, hb, ho, stream), args.steps, stream, flush)
         barrier()
-        tot = sum(te)
-        if world > 1:
-            import torch.distributed as dist
-
-            t = torch.tensor([tot], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
+        tot = max_over_ranks(sum(te))
         nbytes = int(b.nbytes)
         e2e = {"value": applies / (tot / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
-    # per-kernel durations (library events on the launching stream), K more steps
+    # per-kernel durations (library events on the launching stream), a few more steps
     ctx.set_kernel_timing(True)
     kstats = []
-    for _ in range(args.steps):
+    for _ in range(min(args.steps, 3)):
         flush.zero_()
         kstats.append(step())
     torch.cuda.synchronize()
@@ -389,25 +495,31 @@ def run_ours(args, wl):
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "strong" if nodes_split else "weak",
         "vs_baseline": None, "dtype": DTYPES[mode], "data": "synthetic",
         "config": config_dict(args, wl, mode), "clocks": clocks, "e2e": e2e,
         "gpu_launches": int(sum(s["launches"] for s in stats)), "roofline": roof, "kernels": kernels,
         "solver": {"iterations": stats[-1]["iterations"], "max_residual": stats[-1]["max_residual"],
                    "error_bound": stats[-1]["error_bound"], "converged": stats[-1]["converged"],
-                   "spectrum": spec},
+                   "lanczos_spectrum": spec},
     }
-    if mode in ("mixed", "f32x2") and args.compare_steps > 0 and not capped:
-        line[f"{mode}_vs_fp64"] = compare_fp64(ctx, wl, bd, out, nsrc, stream, flush, args.compare_steps,
-                                             total_ms / args.steps)
+    if not capped and not nodes_split and args.compare_steps > 0:
+        for other in wl.get("compare", ()):
+            if other != mode:
+                # the refinement form takes several seconds per step at full size: one timed step
+                k = 1 if other == "mixed" else args.compare_steps
+                line[f"{other}_vs_{mode}"] = compare_mode(ctx, wl, other, bd, out, nsrc, stream, flush, k,
+                                                         total_ms / args.steps, max_iter)
+    if wl.get("dslash") and not args.no_dslash:
+        line["dslash_fp32"] = measure_dslash_fp32(ctx, wl, nsrc, args.steps, flush, args.warmup)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         z, c, c0 = ctx.get_contour()
-        stride = max(1, wl["n_q"] // 16)
-        dt, nn, threads = oracle_sample(U, b[0], z, c, c0, stride)
-        per_apply = dt * len(z) / nn
-        line["cpu_baseline"] = {"value": 1.0 / per_apply, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                "sample": f"source 0, {nn} of {len(z)} nodes (every {stride}th), per-node CGNR to "
-                                          f"1e-13 and weighted sum; time scaled by {len(z)}/{nn}"}
+        t_it = oracle_iteration_seconds(U, b[0])
+        samp = OracleSample(U, b[0], z, c, c0, int(np.clip(15.0 / t_it, 10, 4000)))
+        cb = samp.describe()
+        cb.update({"value": samp.applies_per_s(), "unit": UNIT, "kind": "oracle"})
+        line["cpu_baseline"] = cb
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -438,35 +550,57 @@ FP64_WORK = {
 }
 
 
-def compare_fp64(ctx, wl, bd, out_mixed, nsrc, stream, flush, steps, mixed_ms):
-    """Same step with the plain FP64 forms: time per step, speed-up of the mixed form and
-    the largest relative difference per source between the mixed and FP64 results."""
+def compare_mode(ctx, wl, other, bd, out_ref, nsrc, stream, flush, steps, ref_ms, max_iter):
+    """The same step in another solver mode: device time per step, speed-up of that mode
+    over the line's mode, and the largest difference per source from the line's result
+    (element-wise, max |a - b| / max |b|, and in norm)."""
     import torch
 
-    res = {"ms_per_step": mixed_ms}
-    ref = None
-    for mode in ("fp64", "fp64_2pass"):
-        o = ctx.opts(mode=mode, tol=wl["tol"])
-        ob = torch.empty_like(bd)
-        ctx.overlap(wl["m_q"], bd, ob, nsrc, o)  # warm-up
-        ts = []
-        for _ in range(steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ctx.overlap(wl["m_q"], bd, ob, nsrc, o)
-            e1.record(stream)
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        ms = sum(ts) / len(ts)
-        res[f"{mode}_ms_per_step"] = ms
-        res[f"speedup_vs_{mode}"] = ms / mixed_ms
-        if ref is None:
-            ref = ob
-    d = (out_mixed - ref).reshape(nsrc, -1).norm(dim=1) / ref.reshape(nsrc, -1).norm(dim=1)
-    res["max_rel_diff_vs_fp64"] = float(d.max().item())
-    return res
+    o = ctx.opts(mode=other, tol=wl["tol"], max_iter=max_iter)
+    ob = torch.empty_like(bd)
+    ctx.overlap(wl["m_q"], bd, ob, nsrc, o)  # warm-up (layouts, graphs, autotuning)
+    ts, st = timed_steps(lambda: ctx.overlap(wl["m_q"], bd, ob, nsrc, o), steps, stream, flush)
+    ms = sum(ts) / len(ts)
+    d = (ob - out_ref).reshape(nsrc, -1)
+    ref = out_ref.reshape(nsrc, -1)
+    elem = (d.abs().amax(dim=1) / ref.abs().amax(dim=1)).max().item()
+    norm = (d.norm(dim=1) / ref.norm(dim=1)).max().item()
+    return {"mode": other, "dtype": DTYPES[other], "ms_per_step": ms, "steps": steps,
+            "speedup": ref_ms / ms, "max_rel_diff_elementwise": elem, "max_rel_diff_norm": norm,
+            "iterations": st[-1]["iterations"], "converged": st[-1]["converged"]}
+
+
+def measure_dslash_fp32(ctx, wl, nrhs, steps, flush, warmup):
+    """H_W on nrhs FP32 right-hand sides with the autotuned stencil (ov_apply_HW, OV_FP32):
+    device time per stencil launch from the library's events on the launching stream, and
+    algorithmic bytes (12-real links once, each RHS read and written once) over it."""
+    import torch
+
+    from paper_2204_01583_gb300 import lib
+    import synthetic as S
+
+    dims = wl["dims"]
+    V = int(np.prod(dims))
+    psi = torch.from_numpy(S.gaussian_spinor(dims, 5, n=nrhs).astype(np.complex64)).cuda()
+    o = torch.empty_like(psi)
+    ctx.set_hw32_variant(-1)
+    for _ in range(max(warmup, 1)):
+        ctx.apply_HW(psi, o, nrhs, lib.OV_FP32)  # the first call autotunes
+    torch.cuda.synchronize()
+    ctx.set_kernel_timing(True)
+    for _ in range(steps):
+        flush.zero_()
+        ctx.apply_HW(psi, o, nrhs, lib.OV_FP32)
+    torch.cuda.synchronize()
+    n, ms = ctx.kernel_times()["hw_kernel"]
+    ctx.set_kernel_timing(False)
+    per = ms / n / 1e3
+    by = V * (48 * 4 + nrhs * 48 * 4)
+    hbm, src = hbm_peak()
+    return {"rhs": nrhs, "us_per_launch": per * 1e6, "bytes_per_launch": by, "gbs": by / per / 1e9,
+            "peak_gbs": hbm, "peak_source": src, "frac": by / per / 1e9 / hbm,
+            "bytes": "12-real FP32 links once (48 reals/site) + 48 FP32 reals/site per RHS in and out",
+            "l2": "256 MiB buffer written between launches"}
 
 
 def roofline(wl, mode, ktimes, kstats, nsrc):

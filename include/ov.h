@@ -138,29 +138,44 @@ typedef struct {
   int steps;             /* Lanczos steps taken                                          */
 } ov_spectrum;
 
-/* Create a context on CUDA device `device` for a lattice of size dims.
- * bc_t: +1 periodic, -1 antiperiodic time.  r must be 1.0.
- * Errors: INVALID_ARG (dims < 1, |bc_t| != 1, r != 1), CUDA, OUT_OF_MEMORY. */
+/* Create a context on CUDA device `device` for a lattice of size dims: the geometry,
+ * boundary conditions, Wilson parameter r and mass -m0 of D_W(-m0) in Eq. 1 (the paper
+ * fixes none of them; "Numerical experiments" uses m0 = 1 on 8^4).
+ * bc_t: +1 periodic, -1 antiperiodic time.  r must be 1.0.  The context owns nothing
+ * the caller passes later.
+ * Errors: INVALID_ARG (dims < 1, V > 2^28, |bc_t| != 1, r != 1, m0 not finite), CUDA,
+ * OUT_OF_MEMORY. */
 int ov_create(ov_ctx** ctx, const int dims[4], int bc_t, double m0, double r, int device);
 
-/* Release every device and host resource of the context (NULL is accepted). */
+/* Release every device and host resource of the context (NULL is accepted).  Waits for
+ * the context's outstanding work on the device first. */
 int ov_destroy(ov_ctx* ctx);
 
-/* One-line description of the last error on this context (never NULL). */
+/* One-line description of the last error on this context (never NULL; owned by the
+ * context, valid until its next call). */
 const char* ov_last_error(const ov_ctx* ctx);
 
-/* Load the gauge field (canonical layout, V*4*9 complex doubles).  U may be a
- * host (on_device = 0) or device (on_device = 1) pointer; it is not retained.
- * The library keeps FP64 and FP32 structure-of-arrays copies.  Any cached
- * contour placement is invalidated (explicit contours are kept). */
+/* Load the gauge field: the SU(3) links U_mu(x) of the Wilson operator D_W inside H_W
+ * (Eq. 1; the paper's configurations are quenched SU(3) fields, "Numerical
+ * experiments").  Canonical layout U[mu][t][z][y][x][3][3], V*4*9 complex doubles.
+ * U may be a host (on_device = 0) or device (on_device = 1) pointer; it is copied on
+ * `stream` and not retained.  The library keeps FP64, FP32 and double-float
+ * structure-of-arrays copies.  Any cached contour placement is invalidated (explicit
+ * contours are kept).  Errors: INVALID_ARG (null U), OUT_OF_MEMORY, CUDA. */
 int ov_set_gauge(ov_ctx* ctx, const double* U, int on_device, void* stream);
 
-/* out = H_W in for nrhs spinors in the canonical layout, in the given precision
- * (OV_FP64: complex double, OV_FP32: complex float).  in and out must not alias. */
+/* out = H_W in (Eq. 1 and the definition of H_W = gamma5 D_W(-m0) after it) for nrhs
+ * spinors in the canonical layout psi[rhs][t][z][y][x][4][3], device pointers, in the
+ * given precision (OV_FP64: complex double, OV_FP32: complex float).  in and out must
+ * not alias.  nrhs = 0 is a no-op.  Errors: INVALID_ARG, NO_GAUGE, OUT_OF_MEMORY, CUDA. */
 int ov_apply_HW(ov_ctx* ctx, const void* in, void* out, int nrhs, int precision, void* stream);
 
-/* Set an explicit quadrature: S_N = c0 + sum_j c_j (z_j - H)^-1.  z and c point
- * to n interleaved complex doubles on the host; every Im z_j must be nonzero. */
+/* Set an explicit quadrature: S_N = c0 + sum_j c_j (z_j - H)^-1, the weighted sum of
+ * resolvents of Eqs. 5-7 (Eq. 7 gives the nodes z_j and weights rho w_j / N_q of one
+ * ellipse; any list is accepted, e.g. a share of the nodes for a sharded sum).  z and c
+ * point to n interleaved complex doubles on the host (copied); every Im z_j must be
+ * nonzero.  n = 0 is allowed: then S_N = c0 (z and c may be NULL).
+ * Errors: INVALID_ARG (n < 0, null arrays with n > 0, non-finite values, real node). */
 int ov_set_contour(ov_ctx* ctx, int n, const double* z, const double* c, double c0_re, double c0_im);
 
 /* Set the trapezoid rule of Eq. 7 on the ellipse z = gamma + rho (cos t + i alpha sin t),
@@ -173,10 +188,13 @@ int ov_set_contour_ellipse(ov_ctx* ctx, int n_q, double gamma, double rho, doubl
  * on return *n is the node count).  Pass z = c = NULL to query the count. */
 int ov_get_contour(const ov_ctx* ctx, int* n, double* z, double* c, double* c0);
 
-/* Choose a single-contour ellipse of n_q nodes from Lanczos bounds of H_W and H_W^2
- * (`steps` Lanczos steps on each, from a fixed pseudo-random start) and set it on
+/* Choose a single-contour ellipse of n_q nodes (Eq. 7; the paper tunes alpha, rho and
+ * gamma by hand in "Numerical setup for the integration") from Lanczos bounds of H_W and
+ * H_W^2 (`steps` Lanczos steps on each, from a fixed pseudo-random start) and set it on
  * the context.  The ellipse crosses the real axis at 0 and just beyond the upper
- * bound of the spectrum; alpha minimises the predicted method error.  `out` may be NULL. */
+ * bound of the spectrum; alpha minimises the predicted method error.  `out` (may be
+ * NULL) receives the bounds and the ellipse.  Work is enqueued on `stream` and waited
+ * for.  Errors: INVALID_ARG (n_q < 2, steps < 4), NO_GAUGE, OUT_OF_MEMORY, CUDA. */
 int ov_place_contour(ov_ctx* ctx, int n_q, int steps, ov_spectrum* out, void* stream);
 
 /* Zolotarev node set (not in the paper, whose Summary leaves better quadrature rules to
@@ -197,15 +215,24 @@ int ov_set_contour_zolotarev(ov_ctx* ctx, int n_poles, double lambda_min, double
  * out->predicted_error = delta, out->gamma = rho = alpha = 0. */
 int ov_place_zolotarev(ov_ctx* ctx, int n_poles, int steps, ov_spectrum* out, void* stream);
 
-/* out = S_N b for nrhs sources (complex double, canonical layout). */
+/* out = S_N b ~= sgn(H_W) b for nrhs sources: sgn(H_W) = P_+ - P_- (Eq. 3), each
+ * projector a contour integral of the resolvent (Eqs. 4, 5), the resolvents
+ * y_j = (z_j - H_W)^-1 b (Eq. 6) of every node from one shifted Krylov solve, summed
+ * with the quadrature weights of Eq. 7.  b, out: complex double, canonical layout
+ * [rhs][t][z][y][x][4][3], device pointers (host pointers with opts->host_io); the
+ * caller owns both; they must not alias.  stats may be NULL.
+ * Errors: INVALID_ARG, NO_GAUGE, NO_CONTOUR, NOT_CONVERGED (out holds the last
+ * iterate), BREAKDOWN (non-finite recurrence scalar, e.g. NaN in b), OUT_OF_MEMORY, CUDA. */
 int ov_sgn_HW_apply(ov_ctx* ctx, const void* b, void* out, int nrhs, const ov_solve_opts* opts,
                     ov_stats* stats, void* stream);
 
-/* out = D_ov(m_q) b = (1 + m_q)/2 b + (1 - m_q)/2 gamma5 S_N b (Eq. 1). */
+/* out = D_ov(m_q) b = (1 + m_q)/2 b + (1 - m_q)/2 gamma5 S_N b (Eq. 1), S_N b as in
+ * ov_sgn_HW_apply (same arguments, layouts, ownership and errors; m_q must be finite). */
 int ov_overlap_apply(ov_ctx* ctx, double m_q, const void* b, void* out, int nrhs,
                      const ov_solve_opts* opts, ov_stats* stats, void* stream);
 
-/* Gradients of L = Re <eta, S_N b> (one source; FP64 shifted solves whatever opts->mode):
+/* Gradients of L = Re <eta, S_N b> (one source), from the derivative of the resolvents
+ * in Eq. 4, d(z - H)^-1 = (z - H)^-1 dH (z - H)^-1, with adjoint solves at conj(z_j):
  *   grad_b     = S_N^dag eta (complex double spinor): dL = Re <grad_b, db>;
  *   grad_links = dL/d omega_{x,mu,a} for U_mu(x) -> exp(i omega_a lambda_a/2) U_mu(x)
  *                (double [mu][t][z][y][x][8]).
@@ -292,20 +319,25 @@ int ov_set_kernel_timing(ov_ctx* ctx, int enable);
 int ov_kernel_times(ov_ctx* ctx, const char** names, long long* launches, double* total_ms, int cap);
 
 /* out = H_W in without allocating device memory (FP64, canonical layouts; U, in and
- * out are caller-owned device pointers on the current device).  The paper has no
- * counterpart: this serves callers that cannot call cudaMalloc -- a code that hands
- * all of HBM to its own pool up front, a framework whose allocator must not be
- * bypassed, or work enqueued while a stream is being captured into a graph.  It
- * needs no context.  Its staging buffers (structure-of-arrays copies of U, in and
- * out) live in one fixed 16 MiB device array inside the library, which every GPU
- * that loads the library holds until the process exits; a call needs
+ * out are caller-owned device pointers on the current device; in != out).  The paper
+ * has no counterpart: this serves callers that cannot call cudaMalloc -- a code that
+ * hands all of HBM to its own pool up front, or a framework whose allocator must not
+ * be bypassed (an allocation behind its back can fail, or take memory it has promised
+ * elsewhere).  It needs no context.  Its staging buffers (structure-of-arrays copies
+ * of U, in and out) live in one fixed 16 MiB device array inside the library, which
+ * every GPU that loads the library holds until the process exits; a call needs
  * 576 V + 384 V nrhs bytes (V = sites, each part rounded up to 256 B) and larger
  * requests return OV_ERR_SCRATCH_TOO_SMALL.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress, with that device current);
- * make that first call before any stream capture.  Every call on a device shares
- * the one array: calls that overlap on the GPU (different streams, or different
- * host threads) race and must be serialised by the caller.  Nothing in the array
- * needs to start at zero: each call writes all it reads. */
+ * the array's device address (cudaGetSymbolAddress, with that device current) and
+ * keeps it for the life of the process; make that first call before any stream
+ * capture, and do not use the entry point on a device after cudaDeviceReset (the
+ * kept address belongs to the old context).  Every call on a device shares the one
+ * array: calls that overlap on the GPU (different streams, or different host
+ * threads) race and must be serialised by the caller.  Nothing in the array needs to
+ * start at zero: each call writes all it reads.  Errors: INVALID_ARG (null or
+ * aliasing pointers, nrhs < 1, dims < 1, |bc_t| != 1, m0 not finite),
+ * SCRATCH_TOO_SMALL, CUDA (only for this call's own CUDA calls: an error the caller
+ * left pending is neither cleared nor reported). */
 int ov_apply_HW_noalloc(const int dims[4], int bc_t, double m0, const double* U, const void* in, void* out,
                         int nrhs, void* stream);
 

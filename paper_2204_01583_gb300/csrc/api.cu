@@ -166,6 +166,17 @@ const double2* stage_in(ov_ctx* ctx, const void* p, size_t bytes, int host_io, c
   return (const double2*)d;
 }
 
+namespace {
+// out = c0 b: the quadrature with no nodes (a rank of a node-sharded sum that holds
+// none of them contributes only its share of c0)
+__global__ void cscale_kernel(const double2* __restrict__ in, double2* __restrict__ out, double2 c, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = in[t];
+    out[t] = make_double2(c.x * v.x - c.y * v.y, c.x * v.y + c.y * v.x);
+  }
+}
+}  // namespace
+
 // Core of sgn / overlap: canonical b (device) -> S_N b (SoA, workspace).
 int sign_core(ov_ctx* ctx, const double2* b_dev, int nrhs, const ov_solve_opts& o, SolveOut* so, cudaStream_t s,
               double2** s_soa_out, double2* xs) {
@@ -177,6 +188,15 @@ int sign_core(ov_ctx* ctx, const double2* b_dev, int nrhs, const ov_solve_opts& 
   if (st != OV_OK) return st;
   st = launch_pack64(ctx, b_dev, b_soa, nrhs, s);
   if (st != OV_OK) return st;
+  *s_soa_out = s_soa;
+  if (ctx->z.empty()) {
+    cscale_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 152 * 8), 256, 0, s>>>(b_soa, s_soa, ctx->c0, n);
+    OV_CHECK_LAUNCH(ctx, "cscale_kernel");
+    *so = SolveOut();
+    so->converged = 1;
+    so->launches = 3.0;
+    return OV_OK;
+  }
   if (o.mode == OV_MODE_FP64 || xs) {
     st = solve_sign_soa(ctx, b_soa, s_soa, nrhs, o, so, s, xs);
   } else if (o.mode == OV_MODE_FP64_2PASS || o.mode == OV_MODE_FP64_REGEN || o.mode == OV_MODE_F32X2) {
@@ -430,7 +450,8 @@ int ov_apply_HW(ov_ctx* ctx, const void* in, void* out, int nrhs, int precision,
 
 int ov_set_contour(ov_ctx* ctx, int n, const double* z, const double* c, double c0_re, double c0_im) {
   if (!ctx) return OV_ERR_INVALID_ARG;
-  if (n < 1 || !z || !c) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "bad contour arrays");
+  if (n < 0 || (n > 0 && (!z || !c))) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "bad contour arrays");
+  if (!std::isfinite(c0_re) || !std::isfinite(c0_im)) return ctx_fail(ctx, OV_ERR_INVALID_ARG, "non-finite c0");
   std::vector<double2> zz(n), cc(n);
   for (int j = 0; j < n; ++j) {
     zz[j] = make_double2(z[2 * j], z[2 * j + 1]);
@@ -707,7 +728,7 @@ int vjp_core(ov_ctx* ctx, double a_eta, double gsc, double fsc, bool gamma5_eta,
   const int V = ctx->g.V;
   const size_t n12 = (size_t)12 * V;
   const int nq = (int)ctx->z.size();
-  const int chunk = (o.node_chunk > 0 && o.node_chunk < nq) ? o.node_chunk : nq;
+  const int chunk = std::max(1, (o.node_chunk > 0 && o.node_chunk < nq) ? o.node_chunk : nq);
   const double2* etad = stage_in(ctx, eta, sizeof(double2) * n12, o.host_io, "vjp.eta", s, &st);
   const double2* bd = stage_in(ctx, b, sizeof(double2) * n12, o.host_io, "vjp.b", s, &st);
   double2* src2 = (double2*)ws_get(ctx, "vjp.src", sizeof(double2) * 2 * n12, &st);  // [b; eta_s] SoA
@@ -738,8 +759,8 @@ int vjp_core(ov_ctx* ctx, double a_eta, double gsc, double fsc, bool gamma5_eta,
   // Coefficient-space forms: one stored-basis Lanczos pass for both sources, per-node
   // solutions formed from the basis chunk by chunk (no repeated solves).  Falls back to the
   // vector-space form when the basis does not fit.
-  bool coef_done = false;
-  if (o.mode == OV_MODE_FP64_2PASS || o.mode == OV_MODE_FP64_REGEN || o.mode == OV_MODE_F32X2) {
+  bool coef_done = nq == 0;  // no nodes: grad_b = a eta + gsc conj(c0) eta_s, no force
+  if (!coef_done && (o.mode == OV_MODE_FP64_2PASS || o.mode == OV_MODE_FP64_REGEN || o.mode == OV_MODE_F32X2)) {
     std::vector<double2> zh(2 * (size_t)nq), ch(2 * (size_t)nq);
     for (int j = 0; j < nq; ++j) {
       const double2 z = ctx->z[j], c = ctx->c[j];

@@ -1,15 +1,15 @@
 // ov_apply_HW_noalloc: H_W applied without any device allocation.
 //
 // Some callers cannot call cudaMalloc: a lattice code that hands all of HBM to
-// its own memory pool up front, a process whose device memory is managed by a
-// framework allocator it must not bypass, or code enqueued while a CUDA stream
-// is being captured into a graph (cudaMalloc is not a stream operation and is
-// not permitted then).  This entry point needs no context (creating one and
+// its own memory pool up front, or a process whose device memory is managed by a
+// framework allocator it must not bypass (a cudaMalloc behind its back can fail, or
+// take memory the allocator has promised elsewhere).  This entry point needs no context (creating one and
 // loading a gauge field allocate) and no workspace: its staging buffers -- the
 // structure-of-arrays copies of the gauge field and of the input and output
 // spinors that the stencil kernel reads -- live in one fixed device array
 // declared at file scope below.  Every GPU that loads the library holds that
 // array (kNoAllocScratchBytes) until the process exits.
+#include <cmath>
 #include <mutex>
 
 #include "common.cuh"
@@ -33,11 +33,15 @@ std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch on the current device, looked up on the first call
-// for that device (with that device current) and cached.
-int scratch_for_current_device(void** out) {
+// for that device (with that device current) and cached for the life of the process.
+// A cudaDeviceReset rebuilds the device's context and invalidates the cached address:
+// the entry point must not be used on a device after it has been reset.
+// `before` is the error state the caller left pending: a failure here clears only an
+// error of its own.
+int scratch_for_current_device(void** out, cudaError_t before) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    cudaGetLastError();
+    if (before == cudaSuccess) cudaGetLastError();
     return OV_ERR_CUDA;
   }
   std::lock_guard<std::mutex> lk(g_mu);
@@ -45,7 +49,7 @@ int scratch_for_current_device(void** out) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr) {
-      cudaGetLastError();
+      if (before == cudaSuccess) cudaGetLastError();
       return OV_ERR_CUDA;
     }
     g_scratch_ptr[dev] = p;
@@ -100,20 +104,38 @@ int grid_cap(size_t n) {
 
 size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// One launch, its own status (cudaLaunchKernel returns the error of this launch only).
+template <typename... A>
+cudaError_t launch(void (*k)(A...), dim3 grid, dim3 block, cudaStream_t s, A... args) {
+  void* p[] = {(void*)&args...};
+  return cudaLaunchKernel((const void*)k, grid, block, p, 0, s);
+}
+
 }  // namespace
 
 extern "C" int ov_apply_HW_noalloc(const int dims[4], int bc_t, double m0, const double* U, const void* in,
                                    void* out, int nrhs, void* stream) {
   if (!dims || !U || !in || !out || in == out || nrhs < 1) return OV_ERR_INVALID_ARG;
   if (bc_t != 1 && bc_t != -1) return OV_ERR_INVALID_ARG;
-  for (int k = 0; k < 4; ++k)
+  if (!std::isfinite(m0)) return OV_ERR_INVALID_ARG;
+  // V built one factor at a time, so that no product overflows before the size check
+  long long V = 1;
+  for (int k = 0; k < 4; ++k) {
     if (dims[k] < 1) return OV_ERR_INVALID_ARG;
-  const long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+    V *= dims[k];
+    if (V > (1LL << 28)) return OV_ERR_SCRATCH_TOO_SMALL;
+  }
   const size_t gauge_bytes = round256(sizeof(double2) * 4 * 9 * (size_t)V);
-  const size_t spinor_bytes = round256(sizeof(double2) * 12 * (size_t)V * (size_t)nrhs);
-  if (V > (1LL << 28) || gauge_bytes + 2 * spinor_bytes > kNoAllocScratchBytes) return OV_ERR_SCRATCH_TOO_SMALL;
+  if (gauge_bytes > kNoAllocScratchBytes) return OV_ERR_SCRATCH_TOO_SMALL;
+  const size_t per_rhs = sizeof(double2) * 12 * (size_t)V;
+  if ((size_t)nrhs > (kNoAllocScratchBytes - gauge_bytes) / (2 * per_rhs)) return OV_ERR_SCRATCH_TOO_SMALL;
+  const size_t spinor_bytes = round256(per_rhs * (size_t)nrhs);
+  if (gauge_bytes + 2 * spinor_bytes > kNoAllocScratchBytes) return OV_ERR_SCRATCH_TOO_SMALL;
+  // An error the caller left pending (from its own earlier work) is neither cleared nor
+  // reported as this call's: only the status of this call's own CUDA calls counts.
+  const cudaError_t before = cudaPeekAtLastError();
   void* base = nullptr;
-  int st = scratch_for_current_device(&base);
+  int st = scratch_for_current_device(&base, before);
   if (st != OV_OK) return st;
   double2* U_soa = (double2*)base;
   double2* in_soa = (double2*)((unsigned char*)base + gauge_bytes);
@@ -129,10 +151,20 @@ extern "C" int ov_apply_HW_noalloc(const int dims[4], int bc_t, double m0, const
   cudaStream_t s = (cudaStream_t)stream;
   // every byte of the scratch the stencil reads is written first in this call,
   // so nothing carried over from an earlier call is used
-  na_gauge_pack<<<grid_cap((size_t)4 * 9 * V), 256, 0, s>>>((const double2*)U, U_soa, g.V);
-  na_spinor_pack<<<grid_cap((size_t)12 * V * nrhs), 256, 0, s>>>((const double2*)in, in_soa, g.V, nrhs);
-  na_hw<<<dim3((g.V + kNT - 1) / kNT, nrhs), kNT, 0, s>>>(in_soa, out_soa, U_soa, g, 4.0 - m0);
-  na_spinor_unpack<<<grid_cap((size_t)12 * V * nrhs), 256, 0, s>>>(out_soa, (double2*)out, g.V, nrhs);
-  if (cudaGetLastError() != cudaSuccess) return OV_ERR_CUDA;
+  cudaError_t e = launch(na_gauge_pack, dim3(grid_cap((size_t)4 * 9 * V)), dim3(256), s, (const double2*)U, U_soa,
+                         g.V);
+  if (e == cudaSuccess)
+    e = launch(na_spinor_pack, dim3(grid_cap((size_t)12 * V * nrhs)), dim3(256), s, (const double2*)in, in_soa, g.V,
+               nrhs);
+  if (e == cudaSuccess)
+    e = launch(na_hw, dim3((g.V + kNT - 1) / kNT, nrhs), dim3(kNT), s, (const double2*)in_soa, out_soa,
+               (const double2*)U_soa, g, 4.0 - m0);
+  if (e == cudaSuccess)
+    e = launch(na_spinor_unpack, dim3(grid_cap((size_t)12 * V * nrhs)), dim3(256), s, (const double2*)out_soa,
+               (double2*)out, g.V, nrhs);
+  if (e != cudaSuccess) {
+    if (before == cudaSuccess) cudaGetLastError();  // clear this call's own launch error
+    return OV_ERR_CUDA;
+  }
   return OV_OK;
 }

@@ -65,7 +65,9 @@ def sgn_sharded(ctx, b, opts=None, group=None):
     """S_N b with the nodes of ctx's contour split over the ranks of ``group``.
 
     ctx: a ``lib.Context`` on this rank's GPU with the gauge field and the full contour
-    set (identical on every rank).  Returns S_N b on every rank."""
+    set (identical on every rank).  Returns S_N b on every rank.  Every arithmetic step
+    runs in the library (ov_set_contour with this rank's share, ov_sgn_HW_apply); the
+    only exchange is the sum-allreduce."""
     import torch
     import torch.distributed as dist
 
@@ -76,11 +78,9 @@ def sgn_sharded(ctx, b, opts=None, group=None):
     out = torch.empty_like(b)
     nrhs = b.numel() // (12 * ctx.V)
     try:
-        if len(zr):
-            ctx.set_contour(zr, cr, c0r)
-            ctx.sgn(b, out, nrhs, opts)
-        else:
-            out.copy_(c0r * b)
+        # a rank with no nodes sets an empty node list: the library then forms c0_r b
+        ctx.set_contour(zr, cr, c0r)
+        ctx.sgn(b, out, nrhs, opts)
     finally:
         ctx.set_contour(z, c, c0)
     return allreduce_sum(out, group)
