@@ -273,6 +273,7 @@ int ov_destroy(ov_ctx* ctx) {
   graphs_release(ctx);
   ws_release_all(ctx);
   if (ctx->U64) cudaFree(ctx->U64);
+  if (ctx->U64h) cudaFree(ctx->U64h);
   if (ctx->U32) cudaFree(ctx->U32);
   for (auto& p : ctx->pending) {
     cudaEventDestroy(p.a);
@@ -298,7 +299,8 @@ int ov_set_gauge(ov_ctx* ctx, const double* U, int on_device, void* stream) {
   const size_t n = (size_t)4 * ctx->g.V * 9;
   if (!ctx->U64) {
     if (cudaMalloc(&ctx->U64, sizeof(double2) * n) != cudaSuccess ||
-        cudaMalloc(&ctx->U32, sizeof(float2) * n) != cudaSuccess) {
+        cudaMalloc(&ctx->U32, sizeof(float2) * n) != cudaSuccess ||
+        cudaMalloc(&ctx->U64h, sizeof(double2) * n) != cudaSuccess) {
       cudaGetLastError();
       return ctx_fail(ctx, OV_ERR_OUT_OF_MEMORY, "gauge field allocation failed");
     }

@@ -238,14 +238,17 @@ __device__ __forceinline__ void hop_dir(const typename Store<R>::T* __restrict__
 // multiplied in: acc[12] = (upper: s_f u_f + s_b u_b, lower: A_mu^dag (s_b u_b - s_f u_f))
 // with u_f = U_mu(x) h_f, h_f = psi_up(x+mu) - A_mu psi_lo(x+mu), u_b = U_mu(x-mu)^dag h_b,
 // h_b = psi_up(x-mu) + A_mu psi_lo(x-mu) and s_f, s_b the boundary signs (applied as
-// selects).  The hop term of H_W is -1/2 acc.  Against hop_dir this saves 24 of the 216
-// floating-point instructions of a direction, which on GB300's FP64 pipe is time.
+// selects).  The hop term of H_W is -1/2 acc.  The backward link products accumulate
+// onto t u_f (t = s_f s_b), so C = t u_f + u_b comes out of the FMA chain: upper =
+// s_b C, lower from s_b C - 2 s_f u_f (one FMA per real).  On GB300's FP64 pipe every
+// floating-point instruction saved is time: this form issues 72 + 72 FMAs, 24 projection
+// adds and 12 FMAs per direction.
 template <int MU, typename R, bool CG = false>
 __device__ __forceinline__ void hop_dir_unscaled(const typename Store<R>::T* __restrict__ in,
                                                  const typename Store<R>::T* __restrict__ U, const Geom& g,
                                                  int s, const int c[4], Cx<R> acc[12]) {
   const int V = g.V;
-  Cx<R> uh[2][6];  // [hop][spin * 3 + row]
+  Cx<R> uf[6], ub[6];  // [spin * 3 + row]: u_f, then s_b C
   int sg[2];
 #pragma unroll
   for (int dir = 0; dir < 2; ++dir) {
@@ -266,6 +269,11 @@ __device__ __forceinline__ void hop_dir_unscaled(const typename Store<R>::T* __r
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       Cx<R> u0 = {R(0), R(0)}, u1 = {R(0), R(0)};
+      if (dir == 1) {  // start from t u_f, t = s_f s_b
+        const bool flip = sg[0] != sg[1];
+        u0 = flip ? cneg(uf[i]) : uf[i];
+        u1 = flip ? cneg(uf[3 + i]) : uf[3 + i];
+      }
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         const int e = dir == 0 ? (i * 3 + j) : (j * 3 + i);
@@ -273,19 +281,24 @@ __device__ __forceinline__ void hop_dir_unscaled(const typename Store<R>::T* __r
         if (dir == 0) { u0 = cfma(l, h0[j], u0); u1 = cfma(l, h1[j], u1); }
         else { u0 = cfmaconj(l, h0[j], u0); u1 = cfmaconj(l, h1[j], u1); }
       }
-      uh[dir][i] = u0;
-      uh[dir][3 + i] = u1;
+      if (dir == 0) {
+        uf[i] = u0;
+        uf[3 + i] = u1;
+      } else {
+        ub[i] = sg[1] < 0 ? cneg(u0) : u0;
+        ub[3 + i] = sg[1] < 0 ? cneg(u1) : u1;
+      }
     }
   }
+  const R m2 = sg[0] < 0 ? R(2) : R(-2);  // -2 s_f
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     Cx<R> d[2];
 #pragma unroll
     for (int sp = 0; sp < 2; ++sp) {
-      const Cx<R> a = sg[0] < 0 ? cneg(uh[0][sp * 3 + i]) : uh[0][sp * 3 + i];
-      const Cx<R> b = sg[1] < 0 ? cneg(uh[1][sp * 3 + i]) : uh[1][sp * 3 + i];
-      acc[sp * 3 + i] = cadd(a, b);
-      d[sp] = csub(b, a);
+      const Cx<R> f = uf[sp * 3 + i], up = ub[sp * 3 + i];
+      d[sp] = {fma(m2, f.re, up.re), fma(m2, f.im, up.im)};  // s_b u_b - s_f u_f
+      acc[sp * 3 + i] = up;                                  // s_f u_f + s_b u_b
     }
     mulAdag<MU>(d[0], d[1], acc[2 * 3 + i], acc[3 * 3 + i]);
   }
@@ -452,6 +465,23 @@ struct RowOperand<DF> {
   }
 };
 
+// Spin-projection sum psi_up + phase * psi_lo feeding the link-row products.  Double-float:
+// the error-free sum of the leading parts with the low parts added, not renormalised
+// (the products take hi and lo apart: hi * hi exactly, the cross terms rounded, so an
+// unnormalised lo of at most a few ulp(hi) costs no accuracy and saves the final
+// fast two-sum).  Other types: the plain sum.
+template <typename R>
+__device__ __forceinline__ Cx<R> proj_add(Cx<R> a, Cx<R> b) { return cadd(a, b); }
+__device__ __forceinline__ DF df_add_unnormalised(DF a, DF b) {
+  float s, e;
+  df_two_sum(a.hi, b.hi, s, e);
+  return DF(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+template <>
+__device__ __forceinline__ Cx<DF> proj_add<DF>(Cx<DF> a, Cx<DF> b) {
+  return {df_add_unnormalised(a.re, b.re), df_add_unnormalised(a.im, b.im)};
+}
+
 // Phase 1 with one instruction stream for all directions and both hops: mu and the hop
 // are runtime values, A_mu is applied as a permutation and unit phases, and the rows
 // of the link product are a runtime loop that accumulates into shared memory.  Used
@@ -493,8 +523,8 @@ __device__ __forceinline__ void hw_split_phase1_compact(const typename Store<R>:
       const Cx<R> p1 = ld<R, CG>(in + (1 * 3 + col) * (size_t)V + sn);
       const Cx<R> pa = ld<R, CG>(in + (k2 * 3 + col) * (size_t)V + sn);
       const Cx<R> pb = ld<R, CG>(in + (k3 * 3 + col) * (size_t)V + sn);
-      h0[col] = cadd(p0, uphase(pa, qa0 + qd));
-      h1[col] = cadd(p1, uphase(pb, qa1 + qd));
+      h0[col] = proj_add(p0, uphase(pa, qa0 + qd));
+      h1[col] = proj_add(p1, uphase(pb, qa1 + qd));
     }
     RowOperand<R> hop;
     hop.set(h0, h1);
@@ -527,6 +557,25 @@ __device__ __forceinline__ void hw_split_phase1_compact(const typename Store<R>:
       }
     }
   }
+}
+
+// a - (p0 + p1 + p2 + p3) / 2 in double-float with a single renormalisation: the halved
+// leading parts (exact) enter an error-free two-sum chain, every low part and rounding
+// error is summed in one float, then one fast two-sum.  Error a few units of 2^-48 of
+// the largest term, as for the four separate additions it replaces.
+__device__ __forceinline__ DF df_sum5_half(DF a, DF p0, DF p1, DF p2, DF p3) {
+  float s = a.hi, lo = a.lo, e;
+  df_two_sum(s, -0.5f * p0.hi, s, e);
+  lo = __fadd_rn(lo, __fmaf_rn(-0.5f, p0.lo, e));
+  df_two_sum(s, -0.5f * p1.hi, s, e);
+  lo = __fadd_rn(lo, __fmaf_rn(-0.5f, p1.lo, e));
+  df_two_sum(s, -0.5f * p2.hi, s, e);
+  lo = __fadd_rn(lo, __fmaf_rn(-0.5f, p2.lo, e));
+  df_two_sum(s, -0.5f * p3.hi, s, e);
+  lo = __fadd_rn(lo, __fmaf_rn(-0.5f, p3.lo, e));
+  float hi2, lo2;
+  df_two_sum(s, lo, hi2, lo2);
+  return DF(hi2, lo2);
 }
 
 // a - t / 2 (exact halving; one FMA per real for FP64 and FP32)
@@ -566,8 +615,9 @@ __device__ __forceinline__ void hw_split_phase1(const typename Store<R>::T* __re
 }
 
 // Phase 2 for this thread's three components kk = 3 (t >> 5) + {0, 1, 2}; call after
-// __syncthreads().  Returns false for sites beyond V.
-template <typename R, bool CG = false>
+// __syncthreads().  Returns false for sites beyond V.  HALVED: phase 1 ran on links
+// scaled by -1/2, so its partials already carry the hop factor.
+template <typename R, bool CG = false, bool HALVED = false>
 __device__ __forceinline__ bool hw_split_phase2(const typename Store<R>::T* __restrict__ in, const Geom& g,
                                                 int site0, R diag, const Cx<R>* sm, Cx<R> o[3], int* s_out,
                                                 int* k0_out) {
@@ -580,11 +630,26 @@ __device__ __forceinline__ bool hw_split_phase2(const typename Store<R>::T* __re
   for (int q = 0; q < 3; ++q) {
     const int k = 3 * grp + q;
     // diagonal term minus 1/2 the sum of the four unscaled direction partials
-    const Cx<R> dv = cscale(diag, ld<R, CG>(in + k * (size_t)g.V + s));
+    const Cx<R> x = ld<R, CG>(in + k * (size_t)g.V + s);
     Cx<R> t = sm[k * kSplitSites + lane];
+    if constexpr (!std::is_same<R, DF>::value) {
 #pragma unroll
-    for (int mu = 1; mu < 4; ++mu) t = cadd(t, sm[(mu * 12 + k) * kSplitSites + lane]);
-    const Cx<R> v = sub_half(dv, t);
+      for (int mu = 1; mu < 4; ++mu) t = cadd(t, sm[(mu * 12 + k) * kSplitSites + lane]);
+    }
+    Cx<R> v;
+    if constexpr (std::is_same<R, DF>::value) {
+      // diag x - 1/2 (p0 + p1 + p2 + p3) as one double-float sum of five terms: an
+      // error-free two-sum chain of the leading parts, the low parts and errors in one
+      // float, one renormalisation (instead of four double-float additions)
+      const Cx<R> dv = cscale(diag, x);
+      const Cx<R>* pp = sm + k * kSplitSites + lane;
+      v = {df_sum5_half(dv.re, pp[0].re, pp[12 * kSplitSites].re, pp[24 * kSplitSites].re, pp[36 * kSplitSites].re),
+           df_sum5_half(dv.im, pp[0].im, pp[12 * kSplitSites].im, pp[24 * kSplitSites].im, pp[36 * kSplitSites].im)};
+    } else if constexpr (HALVED) {
+      v = {fma(diag, x.re, t.re), fma(diag, x.im, t.im)};
+    } else {
+      v = sub_half(cscale(diag, x), t);
+    }
     o[q] = (k >= 6) ? cneg(v) : v;
   }
   return true;

@@ -11,9 +11,10 @@ namespace {
 
 constexpr int kNT = 128;
 
-// canonical U[mu][site][i][j] -> planes (mu*9 + 3i + j), FP64 and FP32 copies
+// canonical U[mu][site][i][j] -> planes (mu*9 + 3i + j), FP64 and FP32 copies, and the
+// FP64 copy scaled by -1/2 (exact) for the solver stencils
 __global__ void gauge_ingest_kernel(const double2* __restrict__ aos, double2* __restrict__ u64,
-                                    float2* __restrict__ u32, int V) {
+                                    float2* __restrict__ u32, double2* __restrict__ u64h, int V) {
   const size_t n = (size_t)4 * V * 9;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
     const size_t e = t % 9, q = t / 9;
@@ -22,6 +23,7 @@ __global__ void gauge_ingest_kernel(const double2* __restrict__ aos, double2* __
     const size_t o = (mu * 9 + e) * V + site;
     u64[o] = v;
     u32[o] = make_float2((float)v.x, (float)v.y);
+    u64h[o] = make_double2(-0.5 * v.x, -0.5 * v.y);
   }
 }
 
@@ -101,7 +103,7 @@ int launch_gauge_ingest(ov_ctx* ctx, const double2* U_aos, cudaStream_t s) {
   const size_t n = (size_t)4 * ctx->g.V * 9;
   cudaEvent_t ev;
   kt_begin(ctx, KC_LAYOUT, s, &ev);
-  gauge_ingest_kernel<<<grid_for(n, 256), 256, 0, s>>>(U_aos, ctx->U64, ctx->U32, ctx->g.V);
+  gauge_ingest_kernel<<<grid_for(n, 256), 256, 0, s>>>(U_aos, ctx->U64, ctx->U32, ctx->U64h, ctx->g.V);
   kt_end(ctx, KC_LAYOUT, s, ev);
   OV_CHECK_LAUNCH(ctx, "gauge_ingest_kernel");
   return OV_OK;

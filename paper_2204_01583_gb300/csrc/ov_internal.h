@@ -95,6 +95,7 @@ struct ov_ctx {
 
   // gauge field, structure of arrays: element (mu, i, j, site) at [(mu*9 + 3i + j) * V + site]
   double2* U64 = nullptr;
+  double2* U64h = nullptr;  // -1/2 U: the FP64 solver stencils take the hop factor from the links
   float2* U32 = nullptr;
   bool have_gauge = false;
   bool have_c32 = false;               // compressed FP32 links (workspace "gauge.c32") are current

@@ -51,6 +51,10 @@ constexpr int NT2 = 256;  // K2: vector updates
 // the extra warps (16^3x32, 12 sources: 766 / 744 / 734 us per launch at 6 / 7 / 8).
 template <typename R>
 constexpr int k1_min_blocks() { return std::is_same<R, DF>::value ? 8 : 4; }
+// FP64 solves read the link copy scaled by -1/2 (the hop factor of D_W), so phase 2 adds
+// the partials to the diagonal term without a multiplication
+template <typename R>
+constexpr bool kHalvedLinks = std::is_same<R, double>::value;
 
 struct SrcState {
   double bnorm;   // ||b||
@@ -68,8 +72,8 @@ struct SrcState {
   // derived once per iteration by the block that updates the norms (not per thread):
   double inv_n;   // 1 / ||U_i||
   double cm;      // ||U_i|| / ||U_{i-1}|| (0 at i = 1)
-  float df[6];    // inv_n, cm, alpha as double-float (hi, lo) pairs
-  int pad2_;
+  double alpha_n; // alpha_i / ||U_i||: U_{i+1} = w - alpha_n U_i in one FMA per real
+  float df[8];    // inv_n, cm, alpha, alpha_n as double-float (hi, lo) pairs
 };
 
 // exact double-float split of an FP64 value: hi = rn(x), lo = rn(x - hi)
@@ -103,7 +107,7 @@ __device__ __forceinline__ DF scal<DF>(double, const float* d) { return DF(d[0],
 // Per-iteration scalars of the regeneration pass, in the vector arithmetic type.
 template <typename R>
 struct RegenRec {
-  R inv_n, cm, alpha, pad;
+  R inv_n, cm, alpha, alpha_n;
   Cx<R> g;
 };
 
@@ -121,7 +125,15 @@ struct SolveParams {
   int vec_shifts;  // 1: per-node direction vectors and the weighted sum in K2; 0: scalars only
   int nslots;      // Lanczos vector slots per source: 3 (ring, slot i % 3) or a stored basis (slot i)
   int store;       // 1: slot i holds U_i for every i (basis kept for a later combination)
+  // 1 (scalar-only forms): the per-node LDL^T rows and stopping tests run in
+  // node_check_kernel every kNodeCheck iterations from the recorded alpha_i, beta_i,
+  // not in the last blocks of K1 and K2 (which then only form alpha_i and beta_i)
+  int defer_nodes;
 };
+
+// Iterations between per-node stopping checks of the scalar-only forms: a source runs at
+// most kNodeCheck - 1 iterations past the one where its last node met tol.
+constexpr int kNodeCheck = 8;
 
 // Per-node coefficients l_{i-1}, c_j zeta_i, zeta_i of the vector-space update, stored
 // per iteration by K1's last block: FP64 for FP64 and FP32 vectors (converted where
@@ -210,10 +222,11 @@ template <typename R>
 __device__ __forceinline__ Cx<R> lz_v(Cx<R> u, R inv_n) {
   return {rmul(inv_n, u.re), rmul(inv_n, u.im)};
 }
-// U_{i+1} = w - alpha_i v_i
+// U_{i+1} = w - alpha_i v_i = w - (alpha_i / ||U_i||) U_i, one FMA per real with the
+// scalar alpha_n = alpha_i / ||U_i|| (the FP64 pipe bounds these kernels)
 template <typename R>
-__device__ __forceinline__ Cx<R> lz_next(Cx<R> w, Cx<R> v, R alpha) {
-  return {rfma(-alpha, v.re, w.re), rfma(-alpha, v.im, w.im)};
+__device__ __forceinline__ Cx<R> lz_next(Cx<R> w, Cx<R> u, R alpha_n) {
+  return {rfma(-alpha_n, u.re, w.re), rfma(-alpha_n, u.im, w.im)};
 }
 
 // Per-thread partial of an inner product.  FP64 and FP32 vectors: an FP64 sum.
@@ -223,7 +236,10 @@ template <typename R>
 struct Acc {
   using T = double;
   __device__ __forceinline__ static T zero() { return 0.0; }
+  // FP64 vectors: two FMAs per complex (the FP64 pipe is the bound); FP32 vectors: the
+  // products in FP64
   __device__ __forceinline__ static T dot(T acc, Cx<R> u, Cx<R> w) {
+    if constexpr (std::is_same<R, double>::value) return fma(u.im, w.im, fma(u.re, w.re, acc));
     return acc + ((double)u.re * (double)w.re + (double)u.im * (double)w.im);
   }
   __device__ __forceinline__ static double get(T acc) { return acc; }
@@ -351,7 +367,7 @@ __global__ void __launch_bounds__(NT1, k1_min_blocks<R>()) lanczos_hw_kernel(Sol
     __syncthreads();
     Cx<R> o[3];
     int s, k0;
-    if (hw_split_phase2<R>(Ui, a.g, site0, a.diag, sm, o, &s, &k0)) {
+    if (hw_split_phase2<R, false, kHalvedLinks<R>>(Ui, a.g, site0, a.diag, sm, o, &s, &k0)) {
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const size_t e = (k0 + q) * (size_t)V + s;
@@ -377,7 +393,11 @@ __global__ void __launch_bounds__(NT1, k1_min_blocks<R>()) lanczos_hw_kernel(Sol
     a.cnt[2 * r] = 0;
     const double alpha = tot * inv_n;
     S->alpha = alpha;
-    if constexpr (std::is_same<R, DF>::value) df_split(alpha, S->df + 4);
+    S->alpha_n = alpha * inv_n;
+    if constexpr (std::is_same<R, DF>::value) {
+      df_split(alpha, S->df + 4);
+      df_split(S->alpha_n, S->df + 6);
+    }
     alpha_sh = alpha;
     if (a.hist_a) a.hist_a[(size_t)r * a.prm->max_iter + (i - 1)] = alpha;
     if (!isfinite(alpha)) {
@@ -387,7 +407,7 @@ __global__ void __launch_bounds__(NT1, k1_min_blocks<R>()) lanczos_hw_kernel(Sol
   }
   __syncthreads();
   const double alpha = alpha_sh;
-  if (!isfinite(alpha)) return;
+  if (!isfinite(alpha) || a.prm->defer_nodes) return;
   // per-node LDL^T row i (one thread per node) and the ordered active list
   const int ns = a.prm->nshift;
   const double beta_prev = S->n_cur;  // beta_{i-1} = ||U_i|| (i >= 2)
@@ -457,14 +477,16 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
   const T* Ui = base + lz_slot(a.prm, i) * n12;
   T* W = base + lz_slot(a.prm, i + 1) * n12;
   const int na = a.prm->vec_shifts ? S->n_act : 0;
-  const R inv_nR = scal<R>(S->inv_n, S->df + 0), alphaR = scal<R>(S->alpha, S->df + 4);
+  const R inv_nR = scal<R>(S->inv_n, S->df + 0), anR = scal<R>(S->alpha_n, S->df + 6);
   typename Acc<R>::T nrm = Acc<R>::zero();
   // grid-stride: a few blocks per source (fewer partials and atomics than one block per chunk)
   for (size_t e = (size_t)blockIdx.x * NT2 + threadIdx.x; e < n12; e += (size_t)gridDim.x * NT2) {
-    const Cx<R> v = lz_v<R>(ld<R>(Ui + e), inv_nR);
-    const Cx<R> u = lz_next<R>(ld<R>(W + e), v, alphaR);
+    const Cx<R> ui = ld<R>(Ui + e);
+    const Cx<R> u = lz_next<R>(ld<R>(W + e), ui, anR);
     st<R>(W + e, u);
     nrm = Acc<R>::dot(nrm, u, u);
+    Cx<R> v = ui;  // v_i = U_i / ||U_i||, read only by the per-node direction updates
+    if (na > 0) v = lz_v<R>(ui, inv_nR);
     double sre = 0.0, sim = 0.0;      // weighted sum over nodes: FP64 (FP64, FP32 vectors)
     Cx<R> sdf = {R(0), R(0)};          // or double-float (double-float vectors)
     const int* idx = a.act_idx + (size_t)r * ns;
@@ -528,8 +550,9 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
   const double tol = a.tol_src ? a.tol_src[r] : a.prm->tol;
   const double tol2 = tol * tol;
   const double b2n = nrm2 * S->inv_b2;
+  const bool defer = a.prm->defer_nodes != 0;
   int still = 0;
-  for (int j0 = 0; j0 < ns; j0 += NT2) {
+  for (int j0 = 0; j0 < ns && !defer; j0 += NT2) {
     const int j = j0 + threadIdx.x;
     bool act = false;
     if (j < ns) {
@@ -556,10 +579,84 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
   set_norm_scalars<R>(S);
   if (beta == 0.0) {
     mark_done(S, a.done_count, OV_OK);
-  } else if (ns > 0 && still == 0) {
+  } else if (ns > 0 && still == 0 && !defer) {
     mark_done(S, a.done_count, OV_OK);
   } else if (i >= a.prm->max_iter || (a.prm->store && i + 2 >= a.prm->nslots)) {
     mark_done(S, a.done_count, ns > 0 ? OV_ERR_NOT_CONVERGED : OV_OK);
+  }
+}
+
+// Per-node LDL^T rows and stopping tests of the scalar-only forms (defer_nodes), caught up
+// from the recorded alpha_i, beta_i over the iterations completed since the last check:
+// one thread per node, the same recurrence K1 and K2 run per iteration otherwise,
+//   d_1 = z - alpha_1, omega_1 = ||b||;  l_{i-1} = -beta_{i-1} / d_{i-1},
+//   d_i = z - alpha_i - beta_{i-1}^2 / d_{i-1},  omega_i = -l_{i-1} omega_{i-1};
+//   zeta_i = omega_i / d_i,  node residual |beta_i zeta_i| / ||b||.
+// A node stops at the first iteration that meets tol; a source whose nodes have all
+// stopped is marked done (also one K2 stopped at its iteration limit in that same
+// iteration: its status becomes OV_OK).  Off the per-iteration critical path: K1 and K2
+// keep only their two reductions in the last block.
+template <typename R>
+__global__ void __launch_bounds__(NT1) node_check_kernel(SolveArgs<R> a) {
+  const int r = blockIdx.y;
+  SrcState* S = a.src + r;
+  const int ns = a.prm->nshift;
+  const int mi = a.prm->max_iter;
+  const int upto = S->iter - 1;  // iterations whose alpha_i and beta_i are recorded
+  const double tol = a.tol_src ? a.tol_src[r] : a.prm->tol;
+  const double tol2 = tol * tol;
+  const double* ha = a.hist_a + (size_t)r * mi;
+  const double* hb = a.hist_b + (size_t)r * mi;
+  int still = 0;
+  for (int j0 = 0; j0 < ns; j0 += NT1) {
+    const int j = j0 + threadIdx.x;
+    bool act = false;
+    if (j < ns) {
+      ShiftState& q = a.sh[(size_t)r * ns + j];
+      if (q.active) {
+        const double2 zj = a.z[(size_t)r * ns + j];
+        double2 invd = q.invd, om = q.omega, zeta = q.zeta;
+        double res2 = q.res2;
+        int i = q.last_iter + 1;
+        act = true;
+        for (; i <= upto; ++i) {
+          const double alpha = ha[i - 1], beta = hb[i - 1];
+          double2 d;
+          if (i == 1) {
+            d = make_double2(zj.x - alpha, zj.y);
+            om = make_double2(S->bnorm, 0.0);
+          } else {
+            const double bp = hb[i - 2];  // beta_{i-1} = ||U_i||
+            const double2 lprev = make_double2(-bp * invd.x, -bp * invd.y);
+            const double b2 = bp * bp;
+            d = make_double2(zj.x - alpha - b2 * invd.x, zj.y - b2 * invd.y);
+            om = cmul(make_double2(-lprev.x, -lprev.y), om);
+          }
+          const double inv = __drcp_rn(d.x * d.x + d.y * d.y);
+          invd = make_double2(d.x * inv, -d.y * inv);
+          zeta = cmul(om, invd);
+          res2 = beta * beta * S->inv_b2 * (zeta.x * zeta.x + zeta.y * zeta.y);
+          if (res2 <= tol2 || beta == 0.0) {
+            if (beta == 0.0) res2 = 0.0;
+            act = false;
+            break;
+          }
+        }
+        q.invd = invd;
+        q.omega = om;
+        q.zeta = zeta;
+        q.res2 = res2;
+        q.last_iter = act ? upto : i;
+        q.active = act ? 1 : 0;
+      }
+    }
+    still += __syncthreads_count(act);
+  }
+  if (threadIdx.x == 0 && ns > 0 && still == 0) {
+    if (!S->done)
+      mark_done(S, a.done_count, OV_OK);
+    else if (S->status == OV_ERR_NOT_CONVERGED)
+      S->status = OV_OK;
   }
 }
 
@@ -583,21 +680,22 @@ __global__ void __launch_bounds__(NT1, k1_min_blocks<R>()) lanczos_regen_kernel(
   const T* Um = base + (size_t)((i + 2) % 3) * n12;
   T* W = base + (size_t)((i + 1) % 3) * n12;
   const RegenRec<R> rc = a.rrec[(size_t)r * mi + i - 1];
-  const R inv_nR = rc.inv_n, cmR = rc.cm, alphaR = rc.alpha;
+  const R inv_nR = rc.inv_n, cmR = rc.cm, anR = rc.alpha_n;
   const int site0 = blockIdx.x * kSplitSites;
   hw_split_phase1<R>(Ui, a.U, a.g, site0, sm);
   __syncthreads();
   Cx<R> o[3];
   int s, k0;
-  if (hw_split_phase2<R>(Ui, a.g, site0, a.diag, sm, o, &s, &k0)) {
+  if (hw_split_phase2<R, false, kHalvedLinks<R>>(Ui, a.g, site0, a.diag, sm, o, &s, &k0)) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const int k = k0 + q;
       const size_t e = k * (size_t)V + s;
       const Cx<R> um = (i > 1) ? ld<R>(Um + e) : Cx<R>{R(0), R(0)};
       const Cx<R> w = lz_w<R>(o[q], um, inv_nR, cmR, i == 1);
-      const Cx<R> v = lz_v<R>(ld<R>(Ui + e), inv_nR);
-      st<R>(W + e, lz_next<R>(w, v, alphaR));
+      const Cx<R> ui = ld<R>(Ui + e);
+      const Cx<R> v = lz_v<R>(ui, inv_nR);
+      st<R>(W + e, lz_next<R>(w, ui, anR));
       SumAdd<R>::add(a, (size_t)r * n12 + e, rc.g, v);
     }
   }
@@ -667,7 +765,7 @@ __global__ void __launch_bounds__(NT1, 4) lanczos_coop_kernel(SolveArgs<R> a, in
         Cx<R> o[3];
         int s, k0;
         typename Acc<R>::T dot = Acc<R>::zero();
-        if (hw_split_phase2<R, true>(Ui, a.g, site0, a.diag, sm, o, &s, &k0)) {
+        if (hw_split_phase2<R, true, kHalvedLinks<R>>(Ui, a.g, site0, a.diag, sm, o, &s, &k0)) {
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
             const size_t e = (k0 + q) * (size_t)V + s;
@@ -738,13 +836,12 @@ __global__ void __launch_bounds__(NT1, 4) lanczos_coop_kernel(SolveArgs<R> a, in
       const double inv_n = 1.0 / s_ncur[r];
       const int s = site0 + lane;
       typename Acc<R>::T nrm = Acc<R>::zero();
-      const R inv_nR = (R)inv_n, alphaR = (R)s_alpha[r];
+      const R anR = (R)(s_alpha[r] * inv_n);
       if (s < V) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const size_t e = (3 * grp + q) * (size_t)V + s;
-          const Cx<R> v = lz_v<R>(ld<R, true>(Ui + e), inv_nR);
-          const Cx<R> u = lz_next<R>(ld<R, true>(W + e), v, alphaR);
+          const Cx<R> u = lz_next<R>(ld<R, true>(W + e), ld<R, true>(Ui + e), anR);
           st<R>(W + e, u);
           nrm = Acc<R>::dot(nrm, u, u);
         }
@@ -824,17 +921,19 @@ __global__ void regen_scalars_kernel(SolveArgs<R> a, RegenRec<R>* rec, int nsrc)
     if (i > S->k_final) continue;
     const double n_i = (i == 1) ? S->bnorm : a.hist_b[(size_t)r * mi + i - 2];
     const double n_m = (i <= 2) ? S->bnorm : a.hist_b[(size_t)r * mi + i - 3];
-    float d[6];
+    float d[8];
     const double inv_n = __drcp_rn(n_i), cm = (i > 1) ? n_i / n_m : 0.0, alpha = a.hist_a[(size_t)r * mi + i - 1];
+    const double alpha_n = alpha * inv_n;  // as K1 forms it
     df_split(inv_n, d + 0);
     df_split(cm, d + 2);
     df_split(alpha, d + 4);
+    df_split(alpha_n, d + 6);
     const double2 g = a.gco[(size_t)r * mi + i - 1];
     RegenRec<R> o;
     o.inv_n = scal<R>(inv_n, d + 0);
     o.cm = scal<R>(cm, d + 2);
     o.alpha = scal<R>(alpha, d + 4);
-    o.pad = o.alpha;
+    o.alpha_n = scal<R>(alpha_n, d + 6);
     o.g = cx_from<R>(g.x, g.y);
     rec[t] = o;
   }
@@ -1005,7 +1104,7 @@ inline float4 host_store(double2 v, float4*) {
 
 // link planes and host-side scalar conversion per arithmetic type
 template <typename R> const typename Store<R>::T* solver_links(ov_ctx* ctx);
-template <> const double2* solver_links<double>(ov_ctx* ctx) { return ctx->U64; }
+template <> const double2* solver_links<double>(ov_ctx* ctx) { return ctx->U64h; }  // -1/2 U
 template <> const float2* solver_links<float>(ov_ctx* ctx) { return ctx->U32; }
 template <> const float4* solver_links<DF>(ov_ctx* ctx) { return ctx->Udf; }
 template <typename R> R solver_real(double x) { return (R)x; }
@@ -1022,6 +1121,7 @@ struct SolveWs {
   int nshift = 0;
   int max_iter = 0;  // row length of the per-source histories
   SolveParams* prm_dev = nullptr;
+  bool defer = false;  // per-node recurrences in node_check_kernel (SolveParams::defer_nodes)
 };
 
 // The arguments of sources r0, r0 + 1, ... as a launch of their own sees them: every
@@ -1165,7 +1265,15 @@ int setup_ws(ov_ctx* ctx, int nsrc, int ns, bool want_x, bool want_sacc, bool wa
 }
 
 template <typename R>
-int launch_iteration(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, cudaStream_t s) {
+void launch_node_check(const SolveWs<R>& w, const SolveArgs<R>& a, int nsrc, cudaStream_t s) {
+  node_check_kernel<R><<<dim3(1, nsrc), NT1, 0, s>>>(a);
+}
+
+// One Lanczos iteration (K1, K2); `it` counts iterations from 0 within the loop, and a
+// scalar-only form with deferred node recurrences checks its nodes after every
+// kNodeCheck-th.
+template <typename R>
+int launch_iteration(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, cudaStream_t s, int it) {
   cudaEvent_t ev;
   kt_begin(ctx, KC_LANCZOS_HW, s, &ev);
   lanczos_hw_kernel<R><<<dim3(w.nblk1, nsrc), NT1, 0, s>>>(w.a);
@@ -1173,6 +1281,7 @@ int launch_iteration(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, cudaStream_t s)
   kt_begin(ctx, KC_SHIFT_UPDATE, s, &ev);
   lanczos_update_kernel<R><<<dim3(w.nblk2u, nsrc), NT2, 0, s>>>(w.a);
   kt_end(ctx, KC_SHIFT_UPDATE, s, ev);
+  if (w.defer && (it + 1) % kNodeCheck == 0) launch_node_check<R>(w, w.a, nsrc, s);
   return OV_OK;
 }
 
@@ -1181,7 +1290,10 @@ template <typename R>
 int run_iterations(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, int nshift, int flavour, int max_iter,
                    const ov_solve_opts& o, cudaStream_t s, double* launches) {
   NvtxRange nvtx_("lanczos iterations");
-  const int chunk = o.check_every > 0 ? o.check_every : 32;
+  int chunk = o.check_every > 0 ? o.check_every : 32;
+  // deferred node checks run after every kNodeCheck-th iteration counted from the start,
+  // whatever the chunking: a replayed chunk must span whole check intervals
+  if (w.defer) chunk = (chunk + kNodeCheck - 1) / kNodeCheck * kNodeCheck;
   const bool graph = o.use_graph && !ctx->timing;
   cudaGraphExec_t exec = nullptr;
   if (graph) {
@@ -1200,6 +1312,7 @@ int run_iterations(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, int nshift, int f
             for (int k = 0; k < chunk; ++k) {
               lanczos_hw_kernel<R><<<dim3(w.nblk1, n), NT1, 0, cs>>>(a);
               lanczos_update_kernel<R><<<dim3(w.nblk2u, n), NT2, 0, cs>>>(a);
+              if (w.defer && (k + 1) % kNodeCheck == 0) launch_node_check<R>(w, a, n, cs);
             }
           },
           &exec);
@@ -1211,14 +1324,15 @@ int run_iterations(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, int nshift, int f
   int done_iters = 0;
   while (done_iters < max_iter) {
     const int n = std::min(chunk, max_iter - done_iters);
+    const int nchecks = w.defer ? (done_iters + n) / kNodeCheck - done_iters / kNodeCheck : 0;
     if (graph && n == chunk) {
       cudaError_t e = cudaGraphLaunch(exec, s);
       if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaGraphLaunch");
-      *launches += 2.0 * n * G;
+      *launches += (2.0 * n + nchecks) * G;
     } else {
-      for (int k = 0; k < n; ++k) launch_iteration<R>(ctx, w, nsrc, s);
+      for (int k = 0; k < n; ++k) launch_iteration<R>(ctx, w, nsrc, s, done_iters + k);
       OV_CHECK_LAUNCH(ctx, "lanczos kernels");
-      *launches += 2.0 * n;
+      *launches += 2.0 * n + nchecks;
     }
     done_iters += n;
     cudaError_t e = cudaMemcpyAsync(ctx->host_flag, w.a.done_count, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -1227,6 +1341,11 @@ int run_iterations(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, int nshift, int f
     if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaStreamSynchronize");
     kt_collect(ctx);
     if (*ctx->host_flag >= nsrc) break;
+  }
+  if (w.defer) {  // the iterations since the last check (final node residuals and status)
+    launch_node_check<R>(w, w.a, nsrc, s);
+    OV_CHECK_LAUNCH(ctx, "node_check_kernel");
+    *launches += 1.0;
   }
   return OV_OK;
 }
@@ -1270,7 +1389,9 @@ template <typename R>
 int init_solve(ov_ctx* ctx, SolveWs<R>& w, const double2* b_soa, int nsrc, int ns,
                const std::vector<double2>& zh, const std::vector<double2>& ch, double2 c0,
                double tol, int max_iter, cudaStream_t s, int vec_shifts = 1) {
-  SolveParams prm{tol, max_iter, ns, vec_shifts, w.nslots, w.nslots > 3 ? 1 : 0};
+  // scalar-only forms with nodes defer the per-node recurrences (they record alpha, beta)
+  w.defer = (vec_shifts == 0 && ns > 0 && w.a.hist_a && w.a.hist_b);
+  SolveParams prm{tol, max_iter, ns, vec_shifts, w.nslots, w.nslots > 3 ? 1 : 0, w.defer ? 1 : 0};
   cudaError_t e = cudaMemcpyAsync(w.prm_dev, &prm, sizeof(prm), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy params");
   if (ns > 0) {
