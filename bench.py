@@ -699,7 +699,7 @@ def run_dslash(args, wl):
         # algorithmic link reals: 72 for the forms that read all 9 elements (plain,
         # broadcast, padded pairs), 48 for the 12-real forms; duplicated lanes and padding
         # are not counted
-        link_reals = 48 if comp in (1, 4, 5, 6, 7, 8, 9, 11, 12) else 72
+        link_reals = 48 if comp in (1, 4, 5, 6, 7, 8, 9, 11, 12, 13) else 72
         by = V * (link_reals * s_real + nrhs * 48 * s_real)  # links once per launch; each RHS in + out
         per = ms / n / 1e3
         rows.append({"variant": k, "rhs_tile": rt, "compressed_links": bool(comp), "threads": nt,

@@ -291,7 +291,8 @@ int ov_overlap_solve(ov_ctx* ctx, double m_q, const void* b, void* x, int nrhs, 
  * tile's spinor and x/y link rows with one halo row copied asynchronously into shared
  * memory while the z and t hops read global memory; the centre and x/y hops then read
  * shared memory.  compressed 12: code 9 (128 threads) with row 2 rebuilt once in scalar
- * arithmetic (both lanes of a pair need the same value). */
+ * arithmetic (both lanes of a pair need the same value).  compressed 13: code 12 with
+ * each direction's neighbour spinors and links prefetched into L1 one direction ahead. */
 int ov_set_hw32_variant(ov_ctx* ctx, int k);
 int ov_hw32_variants(int k, int* rhs_tile, int* compressed, int* threads);
 

@@ -351,6 +351,7 @@ constexpr Float4Variant kFloat4Variants[] = {
     {true, 4, 2, 10, 128},  // P, all 9 link elements (padded 5 float4), centre first
     {true, 5, 2, 11, 128},  // P, 12-real compact links, in-plane neighbours staged in shared memory
     {true, 6, 2, 12, 128},  // P, 12-real compact links, centre first, row 2 rebuilt in scalar
+    {true, 7, 2, 13, 128},  // P, the same with each direction's neighbours prefetched into L1
 };
 constexpr int kNFloat4Variants = sizeof(kFloat4Variants) / sizeof(kFloat4Variants[0]);
 

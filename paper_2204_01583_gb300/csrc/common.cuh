@@ -234,16 +234,40 @@ __device__ __forceinline__ void hop_dir(const typename Store<R>::T* __restrict__
   }
 }
 
+// The lower spins of both hops of direction MU: A_mu^dag d with d_s = s_b u_b - s_f u_f
+// = m2 uf_s + ub_s (m2 = -2 s_f, ub = s_f u_f + s_b u_b), each real output one FMA whose
+// sign is folded into its operands (A_mu^dag is a permutation with unit phases).
+template <int MU, typename R>
+__device__ __forceinline__ void lower_from(Cx<R> uf0, Cx<R> ub0, Cx<R> uf1, Cx<R> ub1, R m2, Cx<R>& a0,
+                                           Cx<R>& a1) {
+  auto P = [m2](R f, R u) { return fma(m2, f, u); };    //  d
+  auto N = [m2](R f, R u) { return fma(-m2, f, -u); };  // -d
+  if (MU == 0) {         // A_x^dag d = (i d1, i d0)
+    a0 = {N(uf1.im, ub1.im), P(uf1.re, ub1.re)};
+    a1 = {N(uf0.im, ub0.im), P(uf0.re, ub0.re)};
+  } else if (MU == 1) {  // A_y^dag d = (d1, -d0)
+    a0 = {P(uf1.re, ub1.re), P(uf1.im, ub1.im)};
+    a1 = {N(uf0.re, ub0.re), N(uf0.im, ub0.im)};
+  } else if (MU == 2) {  // A_z^dag d = (i d0, -i d1)
+    a0 = {N(uf0.im, ub0.im), P(uf0.re, ub0.re)};
+    a1 = {P(uf1.im, ub1.im), N(uf1.re, ub1.re)};
+  } else {               // A_t^dag d = d
+    a0 = {P(uf0.re, ub0.re), P(uf0.im, ub0.im)};
+    a1 = {P(uf1.re, ub1.re), P(uf1.im, ub1.im)};
+  }
+}
+
 // Both hops of direction MU for one site, without the -1/2 and boundary-sign factors
 // multiplied in: acc[12] = (upper: s_f u_f + s_b u_b, lower: A_mu^dag (s_b u_b - s_f u_f))
 // with u_f = U_mu(x) h_f, h_f = psi_up(x+mu) - A_mu psi_lo(x+mu), u_b = U_mu(x-mu)^dag h_b,
 // h_b = psi_up(x-mu) + A_mu psi_lo(x-mu) and s_f, s_b the boundary signs (applied as
-// selects).  The hop term of H_W is -1/2 acc.  The backward link products accumulate
-// onto t u_f (t = s_f s_b), so C = t u_f + u_b comes out of the FMA chain: upper =
-// s_b C, lower from s_b C - 2 s_f u_f (one FMA per real).  On GB300's FP64 pipe every
-// floating-point instruction saved is time: this form issues 72 + 72 FMAs, 24 projection
-// adds and 12 FMAs per direction.
-template <int MU, typename R, bool CG = false>
+// selects; SIGNED = false: the links carry them and both are +1).  The hop term of H_W
+// is -1/2 acc (or the links carry the -1/2 as well).  The backward link products
+// accumulate onto t u_f (t = s_f s_b), so C = t u_f + u_b comes out of the FMA chain:
+// upper = s_b C, lower from s_b C - 2 s_f u_f (one FMA per real).  On GB300's FP64
+// pipe every floating-point instruction saved is time: this form issues 72 + 72 FMAs,
+// 24 projection adds and 12 FMAs per direction.
+template <int MU, typename R, bool CG = false, bool SIGNED = true>
 __device__ __forceinline__ void hop_dir_unscaled(const typename Store<R>::T* __restrict__ in,
                                                  const typename Store<R>::T* __restrict__ U, const Geom& g,
                                                  int s, const int c[4], Cx<R> acc[12]) {
@@ -253,6 +277,7 @@ __device__ __forceinline__ void hop_dir_unscaled(const typename Store<R>::T* __r
 #pragma unroll
   for (int dir = 0; dir < 2; ++dir) {
     const int sn = dir == 0 ? nb_fwd(g, s, c, MU, &sg[dir]) : nb_bwd(g, s, c, MU, &sg[dir]);
+    if (!SIGNED) sg[dir] = 1;
     const int sl = dir == 0 ? s : sn;  // link site
     Cx<R> h0[3], h1[3];
 #pragma unroll
@@ -270,7 +295,7 @@ __device__ __forceinline__ void hop_dir_unscaled(const typename Store<R>::T* __r
     for (int i = 0; i < 3; ++i) {
       Cx<R> u0 = {R(0), R(0)}, u1 = {R(0), R(0)};
       if (dir == 1) {  // start from t u_f, t = s_f s_b
-        const bool flip = sg[0] != sg[1];
+        const bool flip = SIGNED && sg[0] != sg[1];
         u0 = flip ? cneg(uf[i]) : uf[i];
         u1 = flip ? cneg(uf[3 + i]) : uf[3 + i];
       }
@@ -285,22 +310,17 @@ __device__ __forceinline__ void hop_dir_unscaled(const typename Store<R>::T* __r
         uf[i] = u0;
         uf[3 + i] = u1;
       } else {
-        ub[i] = sg[1] < 0 ? cneg(u0) : u0;
-        ub[3 + i] = sg[1] < 0 ? cneg(u1) : u1;
+        ub[i] = (SIGNED && sg[1] < 0) ? cneg(u0) : u0;
+        ub[3 + i] = (SIGNED && sg[1] < 0) ? cneg(u1) : u1;
       }
     }
   }
-  const R m2 = sg[0] < 0 ? R(2) : R(-2);  // -2 s_f
+  const R m2 = (SIGNED && sg[0] < 0) ? R(2) : R(-2);  // -2 s_f
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    Cx<R> d[2];
-#pragma unroll
-    for (int sp = 0; sp < 2; ++sp) {
-      const Cx<R> f = uf[sp * 3 + i], up = ub[sp * 3 + i];
-      d[sp] = {fma(m2, f.re, up.re), fma(m2, f.im, up.im)};  // s_b u_b - s_f u_f
-      acc[sp * 3 + i] = up;                                  // s_f u_f + s_b u_b
-    }
-    mulAdag<MU>(d[0], d[1], acc[2 * 3 + i], acc[3 * 3 + i]);
+    acc[i] = ub[i];          // s_f u_f + s_b u_b
+    acc[3 + i] = ub[3 + i];
+    lower_from<MU, R>(uf[i], ub[i], uf[3 + i], ub[3 + i], m2, acc[6 + i], acc[9 + i]);
   }
 }
 
@@ -491,7 +511,7 @@ __device__ __forceinline__ Cx<DF> proj_add<DF>(Cx<DF> a, Cx<DF> b) {
 //   A_mu (l0, l1) = (i^qa0 l_{swap}, i^qa1 l_{1-swap}):  A_x = -i sigma_1 (swap, -i, -i),
 //   A_y = -i sigma_2 (swap, -1, +1), A_z = -i sigma_3 (-i, +i), A_t = 1;
 //   A_mu^dag is the transpose with conjugate phases.
-template <typename R, bool CG>
+template <typename R, bool CG, bool SIGNED = true>
 __device__ __forceinline__ void hw_split_phase1_compact(const typename Store<R>::T* __restrict__ in,
                                                         const typename Store<R>::T* __restrict__ U, const Geom& g,
                                                         int site0, Cx<R>* sm) {
@@ -511,7 +531,7 @@ __device__ __forceinline__ void hw_split_phase1_compact(const typename Store<R>:
 #pragma unroll 1
   for (int dir = 0; dir < 2; ++dir) {
     const bool wrap = dir == 0 ? (cm + 1 == Lm) : (cm == 0);
-    const int sgn = wrap ? bsg : 1;
+    const int sgn = (SIGNED && wrap) ? bsg : 1;
     const int sn = dir == 0 ? (wrap ? s - (Lm - 1) * stm : s + stm) : (wrap ? s + (Lm - 1) * stm : s - stm);
     const int sl = dir == 0 ? s : sn;  // link site
     const int qd = dir == 0 ? 2 : 0;   // forward hop: h = psi_up - A psi_lo, lower gets -A^dag u
@@ -559,20 +579,19 @@ __device__ __forceinline__ void hw_split_phase1_compact(const typename Store<R>:
   }
 }
 
-// a - (p0 + p1 + p2 + p3) / 2 in double-float with a single renormalisation: the halved
-// leading parts (exact) enter an error-free two-sum chain, every low part and rounding
-// error is summed in one float, then one fast two-sum.  Error a few units of 2^-48 of
-// the largest term, as for the four separate additions it replaces.
-__device__ __forceinline__ DF df_sum5_half(DF a, DF p0, DF p1, DF p2, DF p3) {
+// a + f (p0 + p1 + p2 + p3), f = -1/2 (HALF) or 1, in double-float with a single
+// renormalisation: the (exactly) scaled leading parts enter an error-free two-sum chain,
+// every low part and rounding error is summed in one float, then one two-sum.  Error a
+// few units of 2^-48 of the largest term, as for the four separate additions it replaces.
+template <bool HALF>
+__device__ __forceinline__ DF df_sum5(DF a, DF p0, DF p1, DF p2, DF p3) {
+  const DF p[4] = {p0, p1, p2, p3};
   float s = a.hi, lo = a.lo, e;
-  df_two_sum(s, -0.5f * p0.hi, s, e);
-  lo = __fadd_rn(lo, __fmaf_rn(-0.5f, p0.lo, e));
-  df_two_sum(s, -0.5f * p1.hi, s, e);
-  lo = __fadd_rn(lo, __fmaf_rn(-0.5f, p1.lo, e));
-  df_two_sum(s, -0.5f * p2.hi, s, e);
-  lo = __fadd_rn(lo, __fmaf_rn(-0.5f, p2.lo, e));
-  df_two_sum(s, -0.5f * p3.hi, s, e);
-  lo = __fadd_rn(lo, __fmaf_rn(-0.5f, p3.lo, e));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    df_two_sum(s, HALF ? -0.5f * p[k].hi : p[k].hi, s, e);
+    lo = __fadd_rn(lo, HALF ? __fmaf_rn(-0.5f, p[k].lo, e) : __fadd_rn(p[k].lo, e));
+  }
   float hi2, lo2;
   df_two_sum(s, lo, hi2, lo2);
   return DF(hi2, lo2);
@@ -587,12 +606,12 @@ __device__ __forceinline__ Cx<R> sub_half(Cx<R> a, Cx<R> t) {
   return {fma(R(-0.5), t.re, a.re), fma(R(-0.5), t.im, a.im)};
 }
 
-template <typename R, bool CG = false>
+template <typename R, bool CG = false, bool SIGNED = true>
 __device__ __forceinline__ void hw_split_phase1(const typename Store<R>::T* __restrict__ in,
                                                 const typename Store<R>::T* __restrict__ U, const Geom& g,
                                                 int site0, Cx<R>* sm) {
   if constexpr (std::is_same<R, DF>::value) {
-    hw_split_phase1_compact<R, CG>(in, U, g, site0, sm);
+    hw_split_phase1_compact<R, CG, SIGNED>(in, U, g, site0, sm);
     return;
   }
   const int lane = threadIdx.x & 31, mu = threadIdx.x >> 5;
@@ -604,10 +623,10 @@ __device__ __forceinline__ void hw_split_phase1(const typename Store<R>::T* __re
     int c[4];
     site_coords(g, s, c);
     switch (mu) {  // warp-uniform
-      case 0: hop_dir_unscaled<0, R, CG>(in, U, g, s, c, acc); break;
-      case 1: hop_dir_unscaled<1, R, CG>(in, U, g, s, c, acc); break;
-      case 2: hop_dir_unscaled<2, R, CG>(in, U, g, s, c, acc); break;
-      default: hop_dir_unscaled<3, R, CG>(in, U, g, s, c, acc); break;
+      case 0: hop_dir_unscaled<0, R, CG, SIGNED>(in, U, g, s, c, acc); break;
+      case 1: hop_dir_unscaled<1, R, CG, SIGNED>(in, U, g, s, c, acc); break;
+      case 2: hop_dir_unscaled<2, R, CG, SIGNED>(in, U, g, s, c, acc); break;
+      default: hop_dir_unscaled<3, R, CG, SIGNED>(in, U, g, s, c, acc); break;
     }
   }
 #pragma unroll
@@ -643,8 +662,10 @@ __device__ __forceinline__ bool hw_split_phase2(const typename Store<R>::T* __re
       // float, one renormalisation (instead of four double-float additions)
       const Cx<R> dv = cscale(diag, x);
       const Cx<R>* pp = sm + k * kSplitSites + lane;
-      v = {df_sum5_half(dv.re, pp[0].re, pp[12 * kSplitSites].re, pp[24 * kSplitSites].re, pp[36 * kSplitSites].re),
-           df_sum5_half(dv.im, pp[0].im, pp[12 * kSplitSites].im, pp[24 * kSplitSites].im, pp[36 * kSplitSites].im)};
+      v = {df_sum5<!HALVED>(dv.re, pp[0].re, pp[12 * kSplitSites].re, pp[24 * kSplitSites].re,
+                            pp[36 * kSplitSites].re),
+           df_sum5<!HALVED>(dv.im, pp[0].im, pp[12 * kSplitSites].im, pp[24 * kSplitSites].im,
+                            pp[36 * kSplitSites].im)};
     } else if constexpr (HALVED) {
       v = {fma(diag, x.re, t.re), fma(diag, x.im, t.im)};
     } else {

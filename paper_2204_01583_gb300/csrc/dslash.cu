@@ -12,9 +12,13 @@ namespace {
 constexpr int kNT = 128;
 
 // canonical U[mu][site][i][j] -> planes (mu*9 + 3i + j), FP64 and FP32 copies, and the
-// FP64 copy scaled by -1/2 (exact) for the solver stencils
+// FP64 copy for the solver stencils: scaled by -1/2 (exact; the hop factor of D_W) and,
+// on the time links of the last time slice, by the time boundary sign bc_t (a hop
+// across the t boundary in either direction uses exactly that link, so the stencil
+// applies no boundary sign of its own)
 __global__ void gauge_ingest_kernel(const double2* __restrict__ aos, double2* __restrict__ u64,
-                                    float2* __restrict__ u32, double2* __restrict__ u64h, int V) {
+                                    float2* __restrict__ u32, double2* __restrict__ u64h, int V, int Vt,
+                                    double bc_t) {
   const size_t n = (size_t)4 * V * 9;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
     const size_t e = t % 9, q = t / 9;
@@ -23,7 +27,8 @@ __global__ void gauge_ingest_kernel(const double2* __restrict__ aos, double2* __
     const size_t o = (mu * 9 + e) * V + site;
     u64[o] = v;
     u32[o] = make_float2((float)v.x, (float)v.y);
-    u64h[o] = make_double2(-0.5 * v.x, -0.5 * v.y);
+    const double f = (mu == 3 && site >= (size_t)(V - Vt)) ? -0.5 * bc_t : -0.5;
+    u64h[o] = make_double2(f * v.x, f * v.y);
   }
 }
 
@@ -103,7 +108,9 @@ int launch_gauge_ingest(ov_ctx* ctx, const double2* U_aos, cudaStream_t s) {
   const size_t n = (size_t)4 * ctx->g.V * 9;
   cudaEvent_t ev;
   kt_begin(ctx, KC_LAYOUT, s, &ev);
-  gauge_ingest_kernel<<<grid_for(n, 256), 256, 0, s>>>(U_aos, ctx->U64, ctx->U32, ctx->U64h, ctx->g.V);
+  const int Vt = ctx->g.L[0] * ctx->g.L[1] * ctx->g.L[2];  // sites of one time slice
+  gauge_ingest_kernel<<<grid_for(n, 256), 256, 0, s>>>(U_aos, ctx->U64, ctx->U32, ctx->U64h, ctx->g.V, Vt,
+                                                       (double)ctx->g.bc_t);
   kt_end(ctx, KC_LAYOUT, s, ev);
   OV_CHECK_LAUNCH(ctx, "gauge_ingest_kernel");
   return OV_OK;
@@ -182,7 +189,7 @@ int ensure_links_df(ov_ctx* ctx, cudaStream_t s) {
   ctx->Udf = (float4*)ws_get(ctx, "gauge.df", sizeof(float4) * n, &st);
   if (st != OV_OK) return st;
   if (!ctx->have_df) {
-    links_df_kernel<<<grid_for(n, 256), 256, 0, s>>>(ctx->U64, ctx->Udf, n);
+    links_df_kernel<<<grid_for(n, 256), 256, 0, s>>>(ctx->U64h, ctx->Udf, n);  // -1/2 U, signs baked in
     OV_CHECK_LAUNCH(ctx, "links_df_kernel");
     ctx->have_df = true;
   }

@@ -66,7 +66,29 @@ __global__ void links_bcast12_kernel(const float2* __restrict__ u32, float4* __r
 // half spinor and the rebuilt link are live together.
 // CF (centre first): the diagonal term is read before the hops, so that the x and y
 // neighbours, which share its cache lines, follow it through L1.
-template <int LK, int NT, bool CF>
+// Ask L1 for one direction's neighbour data ahead of its use: the 12 component planes of
+// the pair at x + mu and x - mu and the compact 12-real links U_mu(x), U_mu(x - mu)
+// (prefetch.global.L1: no registers are held while the lines arrive).
+__device__ __forceinline__ void pf_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+template <int MU>
+__device__ __forceinline__ void prefetch_dir(const float4* __restrict__ in, const float4* __restrict__ L,
+                                             const Geom& g, int s, const int c[4]) {
+  int sg;
+  const int sf = nb_fwd(g, s, c, MU, &sg), sb = nb_bwd(g, s, c, MU, &sg);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    pf_l1(in + k * (size_t)g.V + sf);
+    pf_l1(in + k * (size_t)g.V + sb);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    pf_l1(L + ((size_t)MU * 3 + k) * g.V + s);
+    pf_l1(L + ((size_t)MU * 3 + k) * g.V + sb);
+  }
+}
+
+// PF: each direction's neighbour data is prefetched into L1 one direction ahead.
+template <int LK, int NT, bool CF, bool PF = false>
 __global__ void __launch_bounds__(NT, 512 / NT) hw_pair12_kernel(const float4* __restrict__ in,
                                                                  float4* __restrict__ out,
                                                                  const float4* __restrict__ L, Geom g, float diag) {
@@ -76,6 +98,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) hw_pair12_kernel(const float4* _
   site_coords(g, s, c);
   const size_t off = (size_t)blockIdx.x * 12 * g.V;
   const float4* inq = in + off;
+  if (PF) prefetch_dir<0>(inq, L, g, s, c);
   const float2 d2 = f2(diag, diag), nd2 = f2(-diag, -diag);
   P2 o[12];
 #pragma unroll
@@ -88,8 +111,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) hw_pair12_kernel(const float4* _
       o[k] = {f2(0.f, 0.f), f2(0.f, 0.f)};
     }
   }
+  if (PF) prefetch_dir<1>(inq, L, g, s, c);
   hop_pair12<0, LK>(inq, L, g, s, c, o);
+  if (PF) prefetch_dir<2>(inq, L, g, s, c);
   hop_pair12<1, LK>(inq, L, g, s, c, o);
+  if (PF) prefetch_dir<3>(inq, L, g, s, c);
   hop_pair12<2, LK>(inq, L, g, s, c, o);
   hop_pair12<3, LK>(inq, L, g, s, c, o);
 #pragma unroll
@@ -250,13 +276,20 @@ static int launch_hw_pair12_tile(ov_ctx* ctx, const float4* in, float4* out, int
 // form 0: broadcast 12-real links (96 B per link); 1: the spin-paired layout's 3 float4
 // (48 B); 2 and 3: form 1 reading the centre first, 128 or 256 threads per block; 4: form
 // 2 with all 9 link elements read (the spin-paired layout's padded 5 float4, 80 B), no
-// rebuild; 5: hw_pair12_tile_kernel; 6: form 2 with row 2 rebuilt in scalar arithmetic.
+// rebuild; 5: hw_pair12_tile_kernel; 6: form 2 with row 2 rebuilt in scalar arithmetic;
+// 7: form 6 with each direction's neighbour data prefetched into L1 one direction ahead
+// (the carveout set to the smallest shared memory, so that L1 holds the prefetched lines).
 int launch_hw_pair12(ov_ctx* ctx, const float4* in, float4* out, int npair, int form, cudaStream_t s) {
   if (form == 5) return launch_hw_pair12_tile(ctx, in, out, npair, s);
   int st = OV_OK;
   const float4* L = form == 0 ? pair_links12(ctx, s, &st) : s4_links(ctx, form != 4, s, &st);
   if (st != OV_OK) return st;
   const int NT = form == 3 ? 256 : 128;
+  if (form == 7) {
+    cudaError_t e = cudaFuncSetAttribute(hw_pair12_kernel<3, 128, true, true>,
+                                         cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaFuncSetAttribute(hw_pair12_kernel)");
+  }
   dim3 grid(npair, (ctx->g.V + NT - 1) / NT);
   const float diag = (float)(4.0 - ctx->m0);
   cudaEvent_t ev;
@@ -271,8 +304,10 @@ int launch_hw_pair12(ov_ctx* ctx, const float4* in, float4* out, int npair, int 
     hw_pair12_kernel<1, 256, true><<<grid, NT, 0, s>>>(in, out, L, ctx->g, diag);
   else if (form == 4)
     hw_pair12_kernel<2, 128, true><<<grid, NT, 0, s>>>(in, out, L, ctx->g, diag);
-  else
+  else if (form == 6)
     hw_pair12_kernel<3, 128, true><<<grid, NT, 0, s>>>(in, out, L, ctx->g, diag);
+  else
+    hw_pair12_kernel<3, 128, true, true><<<grid, NT, 0, s>>>(in, out, L, ctx->g, diag);
   kt_end(ctx, KC_DSLASH, s, ev);
   OV_CHECK_LAUNCH(ctx, "hw_pair12_kernel");
   return OV_OK;

@@ -51,10 +51,11 @@ constexpr int NT2 = 256;  // K2: vector updates
 // the extra warps (16^3x32, 12 sources: 766 / 744 / 734 us per launch at 6 / 7 / 8).
 template <typename R>
 constexpr int k1_min_blocks() { return std::is_same<R, DF>::value ? 8 : 4; }
-// FP64 solves read the link copy scaled by -1/2 (the hop factor of D_W), so phase 2 adds
-// the partials to the diagonal term without a multiplication
+// FP64 and double-float solves read the link copy scaled by -1/2 (the hop factor of D_W) with the time
+// boundary sign on the last time slice's time links, so phase 1 applies no boundary sign
+// and phase 2 adds the partials to the diagonal term without a multiplication
 template <typename R>
-constexpr bool kHalvedLinks = std::is_same<R, double>::value;
+constexpr bool kHalvedLinks = std::is_same<R, double>::value || std::is_same<R, DF>::value;
 
 struct SrcState {
   double bnorm;   // ||b||
@@ -363,7 +364,7 @@ __global__ void __launch_bounds__(NT1, k1_min_blocks<R>()) lanczos_hw_kernel(Sol
       }
     }
   } else {
-    hw_split_phase1<R>(Ui, a.U, a.g, site0, sm);
+    hw_split_phase1<R, false, !kHalvedLinks<R>>(Ui, a.U, a.g, site0, sm);
     __syncthreads();
     Cx<R> o[3];
     int s, k0;
@@ -682,7 +683,7 @@ __global__ void __launch_bounds__(NT1, k1_min_blocks<R>()) lanczos_regen_kernel(
   const RegenRec<R> rc = a.rrec[(size_t)r * mi + i - 1];
   const R inv_nR = rc.inv_n, cmR = rc.cm, anR = rc.alpha_n;
   const int site0 = blockIdx.x * kSplitSites;
-  hw_split_phase1<R>(Ui, a.U, a.g, site0, sm);
+  hw_split_phase1<R, false, !kHalvedLinks<R>>(Ui, a.U, a.g, site0, sm);
   __syncthreads();
   Cx<R> o[3];
   int s, k0;
@@ -760,7 +761,7 @@ __global__ void __launch_bounds__(NT1, 4) lanczos_coop_kernel(SolveArgs<R> a, in
         const double inv_n = 1.0 / s_ncur[r];
         const double cm = (i > 1) ? s_ncur[r] / s_nprev[r] : 0.0;
         const R inv_nR = (R)inv_n, cmR = (R)cm;
-        hw_split_phase1<R, true>(Ui, a.U, a.g, site0, sm);
+        hw_split_phase1<R, true, !kHalvedLinks<R>>(Ui, a.U, a.g, site0, sm);
         __syncthreads();
         Cx<R> o[3];
         int s, k0;

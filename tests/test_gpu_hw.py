@@ -82,13 +82,13 @@ def test_hw_rejects_bad_arguments(gpu_lib):
     assert e.value.code == gpu_lib.OV_ERR_NO_GAUGE
 
 
-@pytest.mark.parametrize("variant", list(range(22)))
+@pytest.mark.parametrize("variant", list(range(23)))
 def test_hw_fp32_variants(gpu_lib, variant):
     """Every FP32 stencil variant (RHS tile, link compression, block size) against the
     oracle, with a right-hand-side count that leaves a ragged last tile."""
     import torch
 
-    assert len(gpu_lib.hw32_variants()) == 22
+    assert len(gpu_lib.hw32_variants()) == 23
     code = gpu_lib.hw32_variants()[variant][1]
     # one xy-plane per block needs Lx Ly = 32k; shared-memory tiles of 128 sites need
     # 128 % Lx == 0 and Ly % (128 / Lx) == 0
