@@ -272,27 +272,16 @@ int ov_overlap_solve(ov_ctx* ctx, double m_q, const void* b, void* x, int nrhs, 
  * size.  k = -1 (default): autotune -- each variant is timed once on the live data per
  * right-hand-side count and the fastest is kept.  ov_hw32_variants returns the number
  * of variants and, for 0 <= k < count, describes variant k.  compressed: 0 plain
- * links, 1 12-real links (structure-of-arrays float2 layout); 2 right-hand-side-paired
- * layout with paired FP32 instructions and broadcast links; 3 and 4 spin-paired float4
- * layout (one 16-byte load per spin pair) with plain (padded) or 12-real links.
- * rhs_tile 0: four threads per site (one per direction), partial sums combined in
- * shared memory.  compressed 5: spin-paired layout with one xy-plane per block
- * (threads reported as 0: Lx Ly of them; needs Lx Ly a multiple of 32, <= 1024), the
- * plane's 12-real links staged in shared memory for rhs_tile right-hand sides and the
- * plane's spinor staged per right-hand side.  compressed 6 and 7: right-hand-side-paired
- * layout with paired FP32 instructions and 12-real links, stored broadcast (re, re, im,
- * im; 96 B per link) or compact (48 B per link, lanes broadcast in registers); row 2 is
- * rebuilt once per link for both right-hand sides of the pair.  compressed 8 and 9: the
- * spin-paired (8) and compact right-hand-side-paired (9) 12-real kernels reading the
- * diagonal term before the hops, with 128 or 256 threads.  compressed 10: code 9 (128
- * threads) reading all 9 link elements (80 B per link with padding; no rebuild).
- * compressed 11: code 9 on tiles of 128 consecutive sites (128 / Lx whole rows of an
- * xy-plane; needs 128 % Lx == 0 and Ly % (128 / Lx) == 0, other lattices skip it), the
- * tile's spinor and x/y link rows with one halo row copied asynchronously into shared
- * memory while the z and t hops read global memory; the centre and x/y hops then read
- * shared memory.  compressed 12: code 9 (128 threads) with row 2 rebuilt once in scalar
- * arithmetic (both lanes of a pair need the same value).  compressed 13: code 12 with
- * each direction's neighbour spinors and links prefetched into L1 one direction ahead. */
+ * links, 1 12-real links (structure-of-arrays float2 layout, the layout the mixed solve
+ * uses); 4: spin-paired float4 layout (one 16-byte load per spin pair) with 12-real
+ * links; 7: right-hand-side-paired layout (one float4 holds a component of two RHS,
+ * paired FP32 instructions act on both) with compact 12-real links (48 B per link, lanes
+ * broadcast in registers); 8 and 9: the spin-paired (8) and paired (9) 12-real kernels
+ * reading the diagonal term before the hops, with 128 or 256 threads; 10: code 9
+ * (128 threads) reading all 9 link elements (80 B per link with padding; no rebuild);
+ * 12: code 9 (128 threads) with row 2 rebuilt once in scalar arithmetic (both lanes of
+ * a pair need the same value).  rhs_tile 0: four threads per site (one per direction),
+ * partial sums combined in shared memory. */
 int ov_set_hw32_variant(ov_ctx* ctx, int k);
 int ov_hw32_variants(int k, int* rhs_tile, int* compressed, int* threads);
 

@@ -322,8 +322,6 @@ int ov_set_gauge(ov_ctx* ctx, const double* U, int on_device, void* stream) {
   ctx->have_gauge = true;
   ctx->coef_iter_hint = 0;
   ctx->have_c32 = false;
-  ctx->have_b32 = false;
-  ctx->have_b12 = false;
   ctx->have_s4 = false;
   ctx->have_df = false;
   return OV_OK;
@@ -334,24 +332,18 @@ int ov_set_gauge(ov_ctx* ctx, const double* U, int on_device, void* stream) {
 // float4 per site and RHS; its buffers alias the paired ones, 6 <= 12 per pair).
 struct Float4Variant {
   bool paired;
-  int form;              // launch_hw_pair12 form, -1: broadcast-link kernel; S: launch_hw32_s4 comp
+  int form;              // P: launch_hw_pair12 form; S: launch_hw32_s4 comp
   int rhs_tile, code, threads;  // as reported by ov_hw32_variants
 };
 constexpr Float4Variant kFloat4Variants[] = {
-    {true, -1, 2, 2, 128},  // P, broadcast 9-element links
-    {false, 0, 1, 3, 128},  // S, padded 5-float4 links
     {false, 1, 1, 4, 128},  // S, 12-real links
-    {false, 2, 6, 5, 0},    // S, one xy-plane per block, links and plane staged in shared memory
-    {true, 0, 2, 6, 128},   // P, 12-real links stored broadcast
     {true, 1, 2, 7, 128},   // P, 12-real links compact
     {false, 3, 1, 8, 128},  // S, 12-real links, centre first
     {false, 4, 1, 8, 256},  // S, 12-real links, centre first, 256 threads per block
     {true, 2, 2, 9, 128},   // P, 12-real compact links, centre first
     {true, 3, 2, 9, 256},   // P, the same with 256 threads per block
     {true, 4, 2, 10, 128},  // P, all 9 link elements (padded 5 float4), centre first
-    {true, 5, 2, 11, 128},  // P, 12-real compact links, in-plane neighbours staged in shared memory
     {true, 6, 2, 12, 128},  // P, 12-real compact links, centre first, row 2 rebuilt in scalar
-    {true, 7, 2, 13, 128},  // P, the same with each direction's neighbours prefetched into L1
 };
 constexpr int kNFloat4Variants = sizeof(kFloat4Variants) / sizeof(kFloat4Variants[0]);
 
@@ -368,7 +360,6 @@ static int fp32_float4_launch(ov_ctx* ctx, int v, const float4* in, float4* out,
   const Float4Variant& f = kFloat4Variants[v];
   const int npair = (nrhs + 1) / 2;
   if (!f.paired) return launch_hw32_s4(ctx, in, out, nrhs, f.form, s);
-  if (f.form < 0) return launch_hw_pair(ctx, in, out, npair, s);
   return launch_hw_pair12(ctx, in, out, npair, f.form, s);
 }
 

@@ -675,3 +675,4 @@ __device__ __forceinline__ bool hw_split_phase2(const typename Store<R>::T* __re
   }
   return true;
 }
+

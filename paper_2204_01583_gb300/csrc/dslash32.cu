@@ -455,74 +455,6 @@ __device__ __forceinline__ void hop_s4(const float4* __restrict__ sp, int sps, c
   }
 }
 
-// out = H_W in on the S4 layout, one xy-plane per block (Lx * Ly threads, one site each).
-// The plane's 12-real links -- forward links of the four directions and the backward
-// z and t links -- are staged in shared memory once per block and serve RB right-hand
-// sides (the link traffic through L2 drops by RB); per RHS the plane's spinor is staged
-// as well, so the x and y neighbours and the centre come from shared memory and only the
-// z and t neighbours are read from global memory.  Backward x and y links are the
-// forward links of the in-plane neighbour.  Shared memory: 24 float4 per site.
-__global__ void hw32_plane_kernel(const float4* __restrict__ in, float4* __restrict__ out,
-                                  const float4* __restrict__ L3, Geom g, float diag, int nrhs, int RB) {
-  extern __shared__ float4 shm[];
-  const int NT = blockDim.x;  // Lx * Ly
-  float4* Lf = shm;           // [mu * 3 + k][NT]
-  float4* Lb = shm + 12 * NT;  // [(z: 0, t: 1) * 3 + k][NT]
-  float4* P = shm + 18 * NT;   // [p][NT]
-  const int tid = threadIdx.x;
-  const int Lx = g.L[0], Ly = g.L[1], Lz = g.L[2], Lt = g.L[3];
-  const int plane = blockIdx.x;  // z + Lz t
-  const int z = plane % Lz, t = plane / Lz;
-  const int V = g.V;
-  const int s = plane * NT + tid;
-  const int x = tid % Lx, y = tid / Lx;
-  const int txp = (x + 1 == Lx) ? tid - (Lx - 1) : tid + 1;
-  const int txm = (x == 0) ? tid + (Lx - 1) : tid - 1;
-  const int typ = (y + 1 == Ly) ? tid - (Ly - 1) * Lx : tid + Lx;
-  const int tym = (y == 0) ? tid + (Ly - 1) * Lx : tid - Lx;
-  const int szp = (z + 1 == Lz) ? s - (Lz - 1) * g.st[2] : s + g.st[2];
-  const int szm = (z == 0) ? s + (Lz - 1) * g.st[2] : s - g.st[2];
-  const int stp = (t + 1 == Lt) ? s - (Lt - 1) * g.st[3] : s + g.st[3];
-  const int stm = (t == 0) ? s + (Lt - 1) * g.st[3] : s - g.st[3];
-  const float ftp = (t + 1 == Lt) ? -0.5f * (float)g.bc_t : -0.5f;
-  const float ftm = (t == 0) ? -0.5f * (float)g.bc_t : -0.5f;
-#pragma unroll
-  for (int q = 0; q < 12; ++q) Lf[q * NT + tid] = __ldg(L3 + (size_t)q * V + s);
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    Lb[k * NT + tid] = __ldg(L3 + (size_t)(2 * 3 + k) * V + szm);
-    Lb[(3 + k) * NT + tid] = __ldg(L3 + (size_t)(3 * 3 + k) * V + stm);
-  }
-  const int r0 = blockIdx.y * RB, r1 = min(nrhs, r0 + RB);
-  for (int r = r0; r < r1; ++r) {
-    const float4* inr = in + (size_t)r * 6 * V;
-    __syncthreads();  // links staged; the previous RHS is done with P
-#pragma unroll
-    for (int p = 0; p < 6; ++p) P[p * NT + tid] = __ldg(inr + (size_t)p * V + s);
-    __syncthreads();
-    Cx<float> acc[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = {0.f, 0.f};
-    hop_s4<0, 0, false>(P + txp, NT, Lf + 0 * 3 * NT + tid, NT, -0.5f, acc);
-    hop_s4<0, 1, false>(P + txm, NT, Lf + 0 * 3 * NT + txm, NT, -0.5f, acc);
-    hop_s4<1, 0, false>(P + typ, NT, Lf + 1 * 3 * NT + tid, NT, -0.5f, acc);
-    hop_s4<1, 1, false>(P + tym, NT, Lf + 1 * 3 * NT + tym, NT, -0.5f, acc);
-    hop_s4<2, 0, true>(inr + szp, V, Lf + 2 * 3 * NT + tid, NT, -0.5f, acc);
-    hop_s4<2, 1, true>(inr + szm, V, Lb + 0 * 3 * NT + tid, NT, -0.5f, acc);
-    hop_s4<3, 0, true>(inr + stp, V, Lf + 3 * 3 * NT + tid, NT, ftp, acc);
-    hop_s4<3, 1, true>(inr + stm, V, Lb + 1 * 3 * NT + tid, NT, ftm, acc);
-    float4* outr = out + (size_t)r * 6 * V;
-#pragma unroll
-    for (int p = 0; p < 6; ++p) {
-      const int sp = p / 3, col = p % 3;
-      const float4 v = P[p * NT + tid];
-      const Cx<float> up = cadd(cscale(diag, Cx<float>{v.x, v.y}), acc[sp * 3 + col]);
-      const Cx<float> lo = cneg(cadd(cscale(diag, Cx<float>{v.z, v.w}), acc[(sp + 2) * 3 + col]));
-      outr[(size_t)p * V + s] = make_float4(up.re, up.im, lo.re, lo.im);
-    }
-  }
-}
-
 // canonical complex64 [rhs][site][12] <-> S4
 __global__ void pack_s4_kernel(const float2* __restrict__ aos, float4* __restrict__ s4, int V, int nrhs) {
   const size_t n = (size_t)nrhs * 6 * V;
@@ -599,31 +531,13 @@ const float4* s4_links(ov_ctx* ctx, bool comp, cudaStream_t s, int* st) {
   return comp ? l3 : l5;
 }
 
-// out = H_W in on the S4 layout; comp selects the 3-float4 (compressed) links, 2 the
-// plane-staged kernel, 3 and 4 the 12-real kernel reading the centre first with 128 or
-// 256 threads per block.
+// out = H_W in on the S4 layout with the 3-float4 (12-real) links; comp 3 and 4: reading
+// the centre first, with 128 or 256 threads per block.
 int launch_hw32_s4(ov_ctx* ctx, const float4* in, float4* out, int nrhs, int comp, cudaStream_t s) {
   int st = OV_OK;
-  const float4* l5 = s4_links(ctx, false, s, &st);
   const float4* l3 = s4_links(ctx, true, s, &st);
   if (st != OV_OK) return st;
   const float diag = (float)(4.0 - ctx->m0);
-  if (comp == 2) {  // one xy-plane per block, links and plane spinor staged in shared memory
-    const int NTp = ctx->g.L[0] * ctx->g.L[1];
-    const size_t shm = sizeof(float4) * 24 * (size_t)NTp;
-    if (NTp % 32 != 0 || NTp > 1024 || shm > 227 * 1024)
-      return ctx_fail(ctx, OV_ERR_INVALID_ARG, "plane-staged FP32 stencil needs Lx*Ly a multiple of 32, <= 1024");
-    cudaError_t e = cudaFuncSetAttribute(hw32_plane_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    if (e != cudaSuccess) return ctx_cuda(ctx, e, "cudaFuncSetAttribute(hw32_plane_kernel)");
-    const int RB = 6;
-    dim3 grid(ctx->g.L[2] * ctx->g.L[3], (nrhs + RB - 1) / RB);
-    cudaEvent_t ev;
-    kt_begin(ctx, KC_DSLASH, s, &ev);
-    hw32_plane_kernel<<<grid, NTp, shm, s>>>(in, out, l3, ctx->g, diag, nrhs, RB);
-    kt_end(ctx, KC_DSLASH, s, ev);
-    OV_CHECK_LAUNCH(ctx, "hw32_plane_kernel");
-    return OV_OK;
-  }
   const int NT = comp == 4 ? 256 : 128;
   dim3 grid((ctx->g.V + NT - 1) / NT, nrhs);
   cudaEvent_t ev;
@@ -632,10 +546,8 @@ int launch_hw32_s4(ov_ctx* ctx, const float4* in, float4* out, int nrhs, int com
     hw32_s4_kernel<true, 256, true><<<grid, NT, 0, s>>>(in, out, l3, ctx->g, diag);
   else if (comp == 3)
     hw32_s4_kernel<true, 128, true><<<grid, NT, 0, s>>>(in, out, l3, ctx->g, diag);
-  else if (comp)
-    hw32_s4_kernel<true, 128, false><<<grid, NT, 0, s>>>(in, out, l3, ctx->g, diag);
   else
-    hw32_s4_kernel<false, 128, false><<<grid, NT, 0, s>>>(in, out, l5, ctx->g, diag);
+    hw32_s4_kernel<true, 128, false><<<grid, NT, 0, s>>>(in, out, l3, ctx->g, diag);
   kt_end(ctx, KC_DSLASH, s, ev);
   OV_CHECK_LAUNCH(ctx, "hw32_s4_kernel");
   return OV_OK;

@@ -99,9 +99,7 @@ struct ov_ctx {
   float2* U32 = nullptr;
   bool have_gauge = false;
   bool have_c32 = false;               // compressed FP32 links (workspace "gauge.c32") are current
-  bool have_b32 = false;               // broadcast FP32 links for the paired layout ("gauge.b32")
   bool have_s4 = false;                // FP32 links for the spin-paired float4 layout
-  bool have_b12 = false;               // broadcast 12-real FP32 links for the paired layout ("gauge.b12")
   float4* Udf = nullptr;               // double-float links (workspace "gauge.df") when have_df
   bool have_df = false;
   std::map<int, int> hw32_choice;      // nrhs -> autotuned FP32 stencil variant
@@ -176,10 +174,8 @@ int launch_pack_s4(ov_ctx* ctx, const float2* aos, float4* s4, int nrhs, cudaStr
 int launch_unpack_s4(ov_ctx* ctx, const float4* s4, float2* aos, int nrhs, cudaStream_t s);
 int launch_hw32_s4(ov_ctx* ctx, const float4* in, float4* out, int nrhs, int comp, cudaStream_t s);
 // paired FP32 layout (pair32.cu)
-const float4* pair_links(ov_ctx* ctx, cudaStream_t s, int* st);
 int launch_pack_pair32(ov_ctx* ctx, const float2* aos, float4* pr, int nrhs, cudaStream_t s);
 int launch_unpack_pair32(ov_ctx* ctx, const float4* pr, float2* aos, int nrhs, cudaStream_t s);
-int launch_hw_pair(ov_ctx* ctx, const float4* in, float4* out, int npair, cudaStream_t s);
 int launch_hw_pair12(ov_ctx* ctx, const float4* in, float4* out, int npair, int form, cudaStream_t s);
 const float4* s4_links(ov_ctx* ctx, bool comp, cudaStream_t s, int* st);
 // out(AoS) = (1+m)/2 b(AoS) + (1-m)/2 gamma5 s(SoA)

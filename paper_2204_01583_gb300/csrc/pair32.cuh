@@ -7,8 +7,8 @@
 // operation of the stencil acts lane-wise on (rhs 2q, rhs 2q+1) with Blackwell's paired
 // FP32 instructions (__ffma2_rn, __fadd2_rn): half the FP32 instructions of a scalar
 // stencil, and no lane shuffles, because the spin and colour algebra is the same on
-// both lanes.  Links are stored broadcast-ready: element (mu, 3i + j, site) is the
-// float4 (re, re, im, im) of U_mu(site)[i][j].
+// both lanes.  Links come in the spin-paired layout's float4 forms (dslash32.cu) and are
+// broadcast to both lanes in registers.
 #pragma once
 
 #include "common.cuh"
@@ -75,108 +75,13 @@ __device__ __forceinline__ void acc_lower(P2& l0, P2& l1, P2 u0, P2 u1, float2 f
   }
 }
 
-// Both hops of direction MU for one site, two right-hand sides, accumulated into
-// acc[12]: upper spins += f u, lower spins += -+ f A^dag u, f = -1/2 * boundary sign.
-// in: pair base (component planes of V float4); L: broadcast links.
-template <int MU>
-__device__ __forceinline__ void hop_pair(const float4* __restrict__ in, const float4* __restrict__ L, const Geom& g,
-                                         int s, const int c[4], P2 acc[12]) {
-  const int V = g.V;
-#pragma unroll
-  for (int dir = 0; dir < 2; ++dir) {
-    int sgn;
-    const int sn = dir == 0 ? nb_fwd(g, s, c, MU, &sgn) : nb_bwd(g, s, c, MU, &sgn);
-    const int sl = dir == 0 ? s : sn;
-    P2 h0[3], h1[3];
-#pragma unroll
-    for (int col = 0; col < 3; ++col) {
-      const P2 p0 = ldp(in + (0 * 3 + col) * (size_t)V + sn);
-      const P2 p1 = ldp(in + (1 * 3 + col) * (size_t)V + sn);
-      const P2 p2 = ldp(in + (2 * 3 + col) * (size_t)V + sn);
-      const P2 p3 = ldp(in + (3 * 3 + col) * (size_t)V + sn);
-      if (dir == 0)
-        proj_pair<MU, -1>(p0, p1, p2, p3, h0[col], h1[col]);
-      else
-        proj_pair<MU, 1>(p0, p1, p2, p3, h0[col], h1[col]);
-    }
-    const float f = -0.5f * (float)sgn;
-    const float2 fu = f2(f, f);
-    // lower spins carry -f (forward, from 1 - gamma) or +f (backward, from 1 + gamma)
-    const float2 fl = dir == 0 ? f2(-f, -f) : f2(f, f);
-    const float2 nfl = dir == 0 ? f2(f, f) : f2(-f, -f);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      // u_s[i] = sum_j M[i][j] h_s[j], M = U (forward) or U^dag (backward):
-      //   forward:  re = sum lr hre - li him,  im = sum lr him + li hre
-      //   backward: re = sum lr hre + li him,  im = sum lr him - li hre
-      float2 a0 = f2(0.f, 0.f), b0 = f2(0.f, 0.f), c0 = f2(0.f, 0.f), e0 = f2(0.f, 0.f);
-      float2 a1 = f2(0.f, 0.f), b1 = f2(0.f, 0.f), c1 = f2(0.f, 0.f), e1 = f2(0.f, 0.f);
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const int e = dir == 0 ? (i * 3 + j) : (j * 3 + i);
-        const float4 l = __ldg(L + (MU * 9 + e) * (size_t)V + sl);
-        const float2 lr = f2(l.x, l.y), li = f2(l.z, l.w);
-        a0 = fma2(lr, h0[j].re, a0);
-        b0 = fma2(li, h0[j].im, b0);
-        c0 = fma2(lr, h0[j].im, c0);
-        a1 = fma2(lr, h1[j].re, a1);
-        b1 = fma2(li, h1[j].im, b1);
-        c1 = fma2(lr, h1[j].im, c1);
-        if (dir == 0) {
-          c0 = fma2(li, h0[j].re, c0);
-          c1 = fma2(li, h1[j].re, c1);
-        } else {
-          e0 = fma2(li, h0[j].re, e0);
-          e1 = fma2(li, h1[j].re, e1);
-        }
-      }
-      P2 u0, u1;
-      if (dir == 0) {
-        u0 = {sub2(a0, b0), c0};
-        u1 = {sub2(a1, b1), c1};
-      } else {
-        u0 = {add2(a0, b0), sub2(c0, e0)};
-        u1 = {add2(a1, b1), sub2(c1, e1)};
-      }
-      acc[0 * 3 + i].re = fma2(fu, u0.re, acc[0 * 3 + i].re);
-      acc[0 * 3 + i].im = fma2(fu, u0.im, acc[0 * 3 + i].im);
-      acc[1 * 3 + i].re = fma2(fu, u1.re, acc[1 * 3 + i].re);
-      acc[1 * 3 + i].im = fma2(fu, u1.im, acc[1 * 3 + i].im);
-      acc_lower<MU>(acc[2 * 3 + i], acc[3 * 3 + i], u0, u1, fl, nfl);
-    }
-  }
-}
-
-// out[12] = (H_W in)(s) for the two right-hand sides of one pair.
-__device__ __forceinline__ void hw_pair_site(const float4* __restrict__ in, const float4* __restrict__ L,
-                                             const Geom& g, int s, float diag, P2 out[12]) {
-  int c[4];
-  site_coords(g, s, c);
-  const float2 d2 = f2(diag, diag);
-#pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    const P2 v = ldp(in + k * (size_t)g.V + s);
-    out[k] = {mul2(d2, v.re), mul2(d2, v.im)};
-  }
-  hop_pair<0>(in, L, g, s, c, out);
-  hop_pair<1>(in, L, g, s, c, out);
-  hop_pair<2>(in, L, g, s, c, out);
-  hop_pair<3>(in, L, g, s, c, out);
-  const float2 m1 = f2(-1.f, -1.f);
-#pragma unroll
-  for (int k = 6; k < 12; ++k) out[k] = {mul2(m1, out[k].re), mul2(m1, out[k].im)};
-}
-
 // ------------------------------------------------------------------------------------
 // The same stencil with 12-real links: rows 0 and 1 of U are read, row 2 is rebuilt as
 // conj(row0 x row1) (U unitary with det U = 1) in paired arithmetic on lane-equal pairs,
 // so one rebuild serves both right-hand sides of the pair (each element is rebuilt
-// where it is used, which keeps one row fewer live).  Two link forms:
-//   BC = true : element (mu, e = 3 row + col, site), e < 6, is the float4 (re, re, im, im)
-//               at (mu * 6 + e) * V + site (96 B per link, no lane moves);
-//   BC = false: the spin-paired layout's 3 float4 per link, (U00, U01), (U02, U10),
-//               (U11, U12) at (mu * 3 + k) * V + site (48 B per link, lanes broadcast in
-//               registers).
+// where it is used, which keeps one row fewer live).  The link form: the spin-paired
+// layout's 3 float4 per link, (U00, U01), (U02, U10), (U11, U12) at (mu * 3 + k) * V +
+// site (48 B per link, lanes broadcast in registers).
 struct B2 {
   float2 re, im;  // both lanes hold the same complex number
 };
@@ -184,20 +89,11 @@ struct B2 {
 __device__ __forceinline__ B2 bc2(float re, float im) { return {f2(re, re), f2(im, im)}; }
 
 // rows 0 and 1 of a 12-real link as lane-equal pairs
-template <bool BC>
 __device__ __forceinline__ void link12_rows(const float4* __restrict__ L, int mu, int V, int site, B2 U[3][3]) {
-  if (BC) {
-#pragma unroll
-    for (int e = 0; e < 6; ++e) {
-      const float4 v = __ldg(L + (mu * 6 + e) * (size_t)V + site);
-      U[e / 3][e % 3] = {f2(v.x, v.y), f2(v.z, v.w)};
-    }
-  } else {
-    const float4* p = L + (size_t)mu * 3 * V + site;
-    const float4 a = __ldg(p), b = __ldg(p + V), c = __ldg(p + 2 * (size_t)V);
-    U[0][0] = bc2(a.x, a.y); U[0][1] = bc2(a.z, a.w); U[0][2] = bc2(b.x, b.y);
-    U[1][0] = bc2(b.z, b.w); U[1][1] = bc2(c.x, c.y); U[1][2] = bc2(c.z, c.w);
-  }
+  const float4* p = L + (size_t)mu * 3 * V + site;
+  const float4 a = __ldg(p), b = __ldg(p + V), c = __ldg(p + 2 * (size_t)V);
+  U[0][0] = bc2(a.x, a.y); U[0][1] = bc2(a.z, a.w); U[0][2] = bc2(b.x, b.y);
+  U[1][0] = bc2(b.z, b.w); U[1][1] = bc2(c.x, c.y); U[1][2] = bc2(c.z, c.w);
 }
 
 // all 9 elements from the spin-paired layout's padded form: 5 float4 per link holding
@@ -251,7 +147,7 @@ __device__ __forceinline__ B2 link12_row2(const B2 U[3][3], int j) {
 // Both hops of direction MU for one site and the two right-hand sides of a pair, with
 // 12-real links.  Upper spins accumulate +f u, lower spins the NEGATED contribution
 // (the caller applies gamma5 = -1 on them by adding -diag psi_lo at the end).
-// LK 0: broadcast 12-real links, 1: compact 12-real links, 2: all 9 elements (padded
+// LK 1: compact 12-real links, 2: all 9 elements (padded
 // 5-float4 form, no rebuild), 3: compact 12-real links with row 2 rebuilt in scalar
 // arithmetic.
 template <int MU, int LK>
@@ -281,7 +177,7 @@ __device__ __forceinline__ void hop_pair12(const float4* __restrict__ in, const 
     else if (LK == 3)
       link12_scalar(L, MU, V, sl, U);
     else
-      link12_rows<LK == 0>(L, MU, V, sl, U);
+      link12_rows(L, MU, V, sl, U);
     const float f = -0.5f * (float)sgn;
     const float2 fu = f2(f, f);
     // lower spins (negated): +f forward (from 1 - gamma), -f backward (from 1 + gamma)
@@ -331,71 +227,3 @@ __device__ __forceinline__ void hop_pair12(const float4* __restrict__ in, const 
   }
 }
 
-// One hop (direction MU; DIR 0: forward, U h with h = psi_up - A psi_lo; 1: backward,
-// U^dag h with h = psi_up + A psi_lo) for one site and a pair of right-hand sides, from
-// shared memory: the neighbour's component k at sp[k * sps], the compact 12-real link's
-// float4 k at lk[k * lks].  Boundary sign +1 (x and y hops); lower spins accumulate
-// negated, as in hop_pair12.
-template <int MU, int DIR>
-__device__ __forceinline__ void hop_pair12_shared(const float4* sp, int sps, const float4* lk, int lks,
-                                                  P2 acc[12]) {
-  P2 h0[3], h1[3];
-#pragma unroll
-  for (int col = 0; col < 3; ++col) {
-    const float4 q0 = sp[(0 * 3 + col) * sps], q1 = sp[(1 * 3 + col) * sps];
-    const float4 q2 = sp[(2 * 3 + col) * sps], q3 = sp[(3 * 3 + col) * sps];
-    const P2 p0 = {f2(q0.x, q0.y), f2(q0.z, q0.w)}, p1 = {f2(q1.x, q1.y), f2(q1.z, q1.w)};
-    const P2 p2 = {f2(q2.x, q2.y), f2(q2.z, q2.w)}, p3 = {f2(q3.x, q3.y), f2(q3.z, q3.w)};
-    if (DIR == 0)
-      proj_pair<MU, -1>(p0, p1, p2, p3, h0[col], h1[col]);
-    else
-      proj_pair<MU, 1>(p0, p1, p2, p3, h0[col], h1[col]);
-  }
-  B2 U[3][3];
-  {
-    const float4 a = lk[0], b = lk[lks], c = lk[2 * lks];
-    U[0][0] = bc2(a.x, a.y); U[0][1] = bc2(a.z, a.w); U[0][2] = bc2(b.x, b.y);
-    U[1][0] = bc2(b.z, b.w); U[1][1] = bc2(c.x, c.y); U[1][2] = bc2(c.z, c.w);
-  }
-  const float2 fu = f2(-0.5f, -0.5f);
-  const float2 fl = DIR == 0 ? f2(-0.5f, -0.5f) : f2(0.5f, 0.5f);
-  const float2 nfl = DIR == 0 ? f2(0.5f, 0.5f) : f2(-0.5f, -0.5f);
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    float2 a0 = f2(0.f, 0.f), b0 = f2(0.f, 0.f), c0 = f2(0.f, 0.f);
-    float2 a1 = f2(0.f, 0.f), b1 = f2(0.f, 0.f), c1 = f2(0.f, 0.f);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const int r = DIR == 0 ? i : j, q = DIR == 0 ? j : i;
-      const B2 l = r < 2 ? U[r][q] : link12_row2(U, q);
-      a0 = fma2(l.re, h0[j].re, a0);
-      a1 = fma2(l.re, h1[j].re, a1);
-      c0 = fma2(l.re, h0[j].im, c0);
-      c1 = fma2(l.re, h1[j].im, c1);
-      if (DIR == 0) {
-        b0 = fma2(l.im, h0[j].im, b0);
-        b1 = fma2(l.im, h1[j].im, b1);
-        c0 = fma2(l.im, h0[j].re, c0);
-        c1 = fma2(l.im, h1[j].re, c1);
-      } else {
-        a0 = fma2(l.im, h0[j].im, a0);
-        a1 = fma2(l.im, h1[j].im, a1);
-        b0 = fma2(l.im, h0[j].re, b0);
-        b1 = fma2(l.im, h1[j].re, b1);
-      }
-    }
-    P2 u0, u1;
-    if (DIR == 0) {
-      u0 = {sub2(a0, b0), c0};
-      u1 = {sub2(a1, b1), c1};
-    } else {
-      u0 = {a0, sub2(c0, b0)};
-      u1 = {a1, sub2(c1, b1)};
-    }
-    acc[0 * 3 + i].re = fma2(fu, u0.re, acc[0 * 3 + i].re);
-    acc[0 * 3 + i].im = fma2(fu, u0.im, acc[0 * 3 + i].im);
-    acc[1 * 3 + i].re = fma2(fu, u1.re, acc[1 * 3 + i].re);
-    acc[1 * 3 + i].im = fma2(fu, u1.im, acc[1 * 3 + i].im);
-    acc_lower<MU>(acc[2 * 3 + i], acc[3 * 3 + i], u0, u1, fl, nfl);
-  }
-}

@@ -480,12 +480,19 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
   const int na = a.prm->vec_shifts ? S->n_act : 0;
   const R inv_nR = scal<R>(S->inv_n, S->df + 0), anR = scal<R>(S->alpha_n, S->df + 6);
   typename Acc<R>::T nrm = Acc<R>::zero();
+  double nrm_im = 0.0;  // FP64 vectors: the imaginary parts in a second, independent FMA chain
   // grid-stride: a few blocks per source (fewer partials and atomics than one block per chunk)
+#pragma unroll 2
   for (size_t e = (size_t)blockIdx.x * NT2 + threadIdx.x; e < n12; e += (size_t)gridDim.x * NT2) {
     const Cx<R> ui = ld<R>(Ui + e);
     const Cx<R> u = lz_next<R>(ld<R>(W + e), ui, anR);
     st<R>(W + e, u);
-    nrm = Acc<R>::dot(nrm, u, u);
+    if constexpr (std::is_same<R, double>::value) {
+      nrm = fma(u.re, u.re, nrm);
+      nrm_im = fma(u.im, u.im, nrm_im);
+    } else {
+      nrm = Acc<R>::dot(nrm, u, u);
+    }
     Cx<R> v = ui;  // v_i = U_i / ||U_i||, read only by the per-node direction updates
     if (na > 0) v = lz_v<R>(ui, inv_nR);
     double sre = 0.0, sim = 0.0;      // weighted sum over nodes: FP64 (FP64, FP32 vectors)
@@ -525,6 +532,7 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
       *Sx = sv;
     }
   }
+  if constexpr (std::is_same<R, double>::value) nrm += nrm_im;
   double bs = Acc<R>::template total<NT2>(nrm, sh);
   if (threadIdx.x == 0) {
     a.part2[(size_t)r * gridDim.x + blockIdx.x] = bs;
