@@ -184,8 +184,10 @@ int ov_set_contour(ov_ctx* ctx, int n, const double* z, const double* c, double 
  * +-gamma, c0 = 0 (2 n_q nodes). */
 int ov_set_contour_ellipse(ov_ctx* ctx, int n_q, double gamma, double rho, double alpha, int form);
 
-/* Copy the current quadrature to host arrays (z, c: room for *n complex doubles;
- * on return *n is the node count).  Pass z = c = NULL to query the count. */
+/* Copy the current quadrature (the nodes and weights of Eqs. 5-7 set on the context) to
+ * host arrays (z, c: room for *n complex doubles; on return *n is the node count).  Pass
+ * z = c = NULL to query the count.  Errors: INVALID_ARG (n NULL, *n too small),
+ * NO_CONTOUR. */
 int ov_get_contour(const ov_ctx* ctx, int* n, double* z, double* c, double* c0);
 
 /* Choose a single-contour ellipse of n_q nodes (Eq. 7; the paper tunes alpha, rho and
@@ -267,7 +269,8 @@ int ov_overlap_solve(ov_ctx* ctx, double m_q, const void* b, void* x, int nrhs, 
                      double tol, int max_iter, ov_stats* stats, void* stream);
 
 /* FP32 stencil selection for ov_apply_HW(OV_FP32) and the FP32 phases of the mixed
- * solve.  Variants differ in right-hand sides per thread (link loads reused across
+ * solve (implementation choices of the H_W stencil of Eq. 1; the paper has no
+ * counterpart).  Variants differ in right-hand sides per thread (link loads reused across
  * them), 12-real link compression (row 2 rebuilt as conj(row0 x row1)) and block
  * size.  k = -1 (default): autotune -- each variant is timed once on the live data per
  * right-hand-side count and the fastest is kept.  ov_hw32_variants returns the number
@@ -285,14 +288,16 @@ int ov_overlap_solve(ov_ctx* ctx, double m_q, const void* b, void* x, int nrhs, 
 int ov_set_hw32_variant(ov_ctx* ctx, int k);
 int ov_hw32_variants(int k, int* rhs_tile, int* compressed, int* threads);
 
-/* enable = 1: the coefficient-space FP64 solve runs its whole iteration loop as one
+/* Launch structure of the Krylov loop (no counterpart in the paper).
+ * enable = 1: the coefficient-space FP64 solve runs its whole iteration loop as one
  * cooperative persistent launch when the grid fits on the GPU (up to 16 sources);
  * enable = 0 (default): one launch per iteration phase, replayed from CUDA graphs
  * (measured faster on GB300 at 8^4: two grid barriers per iteration and L2-only
  * neighbour loads cost more than the launches and reduction tails they remove). */
 int ov_set_persistent(ov_ctx* ctx, int enable);
 
-/* Sources of one call are independent; the per-iteration kernels replayed from a CUDA
+/* Scheduling of independent sources (no counterpart in the paper).
+ * Sources of one call are independent; the per-iteration kernels replayed from a CUDA
  * graph can run as `groups` parallel branches, each over a contiguous block of sources,
  * which fills the launch tails and serial reduction steps of small lattices.  groups = 0
  * (default): one branch per source, at most four, when the stencil grid of all sources
@@ -301,7 +306,7 @@ int ov_set_persistent(ov_ctx* ctx, int enable);
  * Errors: OV_ERR_INVALID_ARG for groups outside [0, 64]. */
 int ov_set_concurrency(ov_ctx* ctx, int groups);
 
-/* Kernel timing: when enabled, the library brackets every launch of its main
+/* Kernel timing (instrumentation; no counterpart in the paper): when enabled, the library brackets every launch of its main
  * kernel classes with CUDA events on the launching stream and accumulates their
  * durations.  ov_kernel_times fills up to `cap` entries (name pointer, launches,
  * total ms) and returns the number of classes.  Disabled by default. */
@@ -331,7 +336,7 @@ int ov_kernel_times(ov_ctx* ctx, const char** names, long long* launches, double
 int ov_apply_HW_noalloc(const int dims[4], int bc_t, double m0, const double* U, const void* in, void* out,
                         int nrhs, void* stream);
 
-/* Library version string. */
+/* Library version string (no counterpart in the paper). */
 const char* ov_version(void);
 
 #ifdef __cplusplus
