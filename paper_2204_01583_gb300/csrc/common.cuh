@@ -61,6 +61,18 @@ __device__ __forceinline__ DF fma(DF a, DF b, DF c) {
   t = __fmaf_rn(a.lo, b.hi, t);
   return df_quick_two_sum(s, t);
 }
+// a * b + c without the final renormalisation (the result's low part may exceed half an
+// ulp of its high part by a few units; fine for a running sum renormalised at the end)
+__device__ __forceinline__ DF fma_unnormalised(DF a, DF b, DF c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float pe = __fmaf_rn(a.hi, b.hi, -p);
+  float s, e;
+  df_two_sum(c.hi, p, s, e);
+  float t = __fadd_rn(__fadd_rn(e, pe), c.lo);
+  t = __fmaf_rn(a.hi, b.lo, t);
+  t = __fmaf_rn(a.lo, b.hi, t);
+  return DF(s, t);
+}
 __device__ __forceinline__ DF& operator+=(DF& a, DF b) { return a = a + b; }
 __device__ __forceinline__ DF& operator-=(DF& a, DF b) { return a = a - b; }
 
@@ -570,10 +582,11 @@ __device__ __forceinline__ void hw_split_phase1_compact(const typename Store<R>:
         a[2 * 3 * kSplitSites] = c2;
         a[3 * 3 * kSplitSites] = c3;
       } else {
-        a[0 * 3 * kSplitSites] = cadd(a[0 * 3 * kSplitSites], c0);
-        a[1 * 3 * kSplitSites] = cadd(a[1 * 3 * kSplitSites], c1);
-        a[2 * 3 * kSplitSites] = cadd(a[2 * 3 * kSplitSites], c2);
-        a[3 * 3 * kSplitSites] = cadd(a[3 * 3 * kSplitSites], c3);
+        // unnormalised (phase 2 sums the four partials with one renormalisation)
+        a[0 * 3 * kSplitSites] = proj_add(a[0 * 3 * kSplitSites], c0);
+        a[1 * 3 * kSplitSites] = proj_add(a[1 * 3 * kSplitSites], c1);
+        a[2 * 3 * kSplitSites] = proj_add(a[2 * 3 * kSplitSites], c2);
+        a[3 * 3 * kSplitSites] = proj_add(a[3 * 3 * kSplitSites], c3);
       }
     }
   }

@@ -251,8 +251,9 @@ template <>
 struct Acc<DF> {
   using T = DF;
   __device__ __forceinline__ static T zero() { return DF(0.f, 0.f); }
+  // running sum unnormalised (renormalised by the block sum)
   __device__ __forceinline__ static T dot(T acc, Cx<DF> u, Cx<DF> w) {
-    return fma(u.im, w.im, fma(u.re, w.re, acc));
+    return fma_unnormalised(u.im, w.im, fma_unnormalised(u.re, w.re, acc));
   }
   __device__ __forceinline__ static double get(T acc) { return (double)acc; }
   // block sum in double-float (fixed tree), one FP64 conversion per block; sh >= NT/32 doubles
@@ -481,9 +482,36 @@ __global__ void __launch_bounds__(NT2) lanczos_update_kernel(SolveArgs<R> a) {
   const R inv_nR = scal<R>(S->inv_n, S->df + 0), anR = scal<R>(S->alpha_n, S->df + 6);
   typename Acc<R>::T nrm = Acc<R>::zero();
   double nrm_im = 0.0;  // FP64 vectors: the imaginary parts in a second, independent FMA chain
+  size_t e0 = (size_t)blockIdx.x * NT2 + threadIdx.x;
+  const size_t gs = (size_t)gridDim.x * NT2;
+  if constexpr (!std::is_same<R, float>::value) {
+    // scalar-only forms (no per-node vectors): four elements per thread in flight, their
+    // loads issued before any arithmetic (the arithmetic and HBM overlap across them)
+    if (na == 0) {
+      constexpr int B = 4;
+      for (; e0 + (B - 1) * gs < n12; e0 += B * gs) {
+        Cx<R> ub[B], wb[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          ub[k] = ld<R>(Ui + e0 + k * gs);
+          wb[k] = ld<R>(W + e0 + k * gs);
+        }
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          const Cx<R> u = lz_next<R>(wb[k], ub[k], anR);
+          st<R>(W + e0 + k * gs, u);
+          if constexpr (std::is_same<R, double>::value) {
+            nrm = fma(u.re, u.re, nrm);
+            nrm_im = fma(u.im, u.im, nrm_im);
+          } else {
+            nrm = Acc<R>::dot(nrm, u, u);
+          }
+        }
+      }
+    }
+  }
   // grid-stride: a few blocks per source (fewer partials and atomics than one block per chunk)
-#pragma unroll 2
-  for (size_t e = (size_t)blockIdx.x * NT2 + threadIdx.x; e < n12; e += (size_t)gridDim.x * NT2) {
+  for (size_t e = e0; e < n12; e += gs) {
     const Cx<R> ui = ld<R>(Ui + e);
     const Cx<R> u = lz_next<R>(ld<R>(W + e), ui, anR);
     st<R>(W + e, u);
@@ -951,8 +979,11 @@ __global__ void regen_scalars_kernel(SolveArgs<R> a, RegenRec<R>* rec, int nsrc)
 // Stored-basis variant of the second pass: sum[r][e] += sum_{i=1..k_r} gw[r][i-1] U_i[e],
 // gw = g_i / ||U_i|| (the basis is stored unnormalised), in the arithmetic of the basis
 // (FP64, or double-float with gw split into double-float pairs on the host); one read
-// of the basis and one FP64 update of the sum per element.
-template <typename R>
+// of the basis and one FP64 update of the sum per element.  REAL: the coefficients are
+// real (a node list closed under conjugation, z_j and conj(z_j) with conj(c_j): T_k is
+// real, so (conj z - T_k)^-1 e_1 = conj((z - T_k)^-1 e_1) and g = sum_j c_j y^j is real),
+// two FMAs per element and basis vector instead of four.
+template <typename R, bool REAL = false>
 __global__ void basis_sum_kernel(const typename Store<R>::T* __restrict__ basis, int nslots,
                                  const typename Store<R>::T* __restrict__ gw, int ldg, const int* __restrict__ kr,
                                  double2* __restrict__ sum, size_t n12) {
@@ -963,7 +994,15 @@ __global__ void basis_sum_kernel(const typename Store<R>::T* __restrict__ basis,
   const typename Store<R>::T* w = gw + (size_t)r * ldg;
   Cx<R> acc = {R(0), R(0)};
   const int k = kr[r];
-  for (int i = 1; i <= k; ++i) acc = cfma(ld<R>(w + i - 1), ld<R>(B + (size_t)i * n12), acc);
+  for (int i = 1; i <= k; ++i) {
+    const Cx<R> wi = ld<R>(w + i - 1), b = ld<R>(B + (size_t)i * n12);
+    if constexpr (REAL) {
+      acc.re = fma(wi.re, b.re, acc.re);
+      acc.im = fma(wi.re, b.im, acc.im);
+    } else {
+      acc = cfma(wi, b, acc);
+    }
+  }
   double2 sv = sum[(size_t)r * n12 + e];
   sv.x += (double)acc.re;
   sv.y += (double)acc.im;
@@ -1639,6 +1678,18 @@ static int solve_sign_stored(ov_ctx* ctx, const double2* b_soa, double2* out_soa
       g[(size_t)r * cap + i].x /= ni;
       g[(size_t)r * cap + i].y /= ni;
     }
+  // a node list closed under conjugation gives real coefficients (up to rounding):
+  // then the sum takes half the multiplications
+  bool real = true;
+  for (int r = 0; r < nsrc && real; ++r) {
+    double gmax = 0.0, imax = 0.0;
+    for (int i = 0; i < kr[r]; ++i) {
+      const double2 v = g[(size_t)r * cap + i];
+      gmax = std::max(gmax, std::hypot(v.x, v.y));
+      imax = std::max(imax, std::fabs(v.y));
+    }
+    real = std::isfinite(gmax) && imax <= 1e-14 * gmax;
+  }
   using T = typename Store<R>::T;
   std::vector<T> gs(g.size());
   for (size_t t = 0; t < g.size(); ++t) gs[t] = host_store(g[t], (T*)nullptr);
@@ -1650,8 +1701,11 @@ static int solve_sign_stored(ov_ctx* ctx, const double2* b_soa, double2* out_soa
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "copy coefficients");
   cudaEvent_t ev;
   kt_begin(ctx, KC_BASIS_SUM, s, &ev);
-  basis_sum_kernel<R><<<dim3((unsigned)((n12 + 255) / 256), nsrc), 256, 0, s>>>(w.a.ring, cap + 3, gd, cap, krd,
-                                                                             w.a.sacc, n12);
+  const dim3 gsum((unsigned)((n12 + 255) / 256), nsrc);
+  if (real)
+    basis_sum_kernel<R, true><<<gsum, 256, 0, s>>>(w.a.ring, cap + 3, gd, cap, krd, w.a.sacc, n12);
+  else
+    basis_sum_kernel<R, false><<<gsum, 256, 0, s>>>(w.a.ring, cap + 3, gd, cap, krd, w.a.sacc, n12);
   kt_end(ctx, KC_BASIS_SUM, s, ev);
   OV_CHECK_LAUNCH(ctx, "basis_sum_kernel");
   so->launches = launches + 3.0;

@@ -350,3 +350,18 @@ def test_empty_contour_is_c0_times_b(gpu_lib):
     out = torch.empty_like(to_dev(b))
     ctx.overlap(0.1, to_dev(b), out, 2)
     assert rel(to_host(out), sign.overlap_from_sign(b, c0 * b, 0.1)) < 1e-15
+
+
+@pytest.mark.parametrize("mode", ["fp64_2pass", "f32x2", "fp64"])
+def test_node_list_not_closed_under_conjugation(gpu_lib, mode):
+    """A node list without conjugate partners gives complex Lanczos-basis coefficients
+    (the stored-basis sum then takes its complex form); parity with the oracle."""
+    dims = (4, 4, 4, 8)
+    ctx, U = make_ctx(gpu_lib, dims, 0.4, 1501)
+    z = np.array([1.0 + 1.5j, -2.0 + 0.8j, 4.0 - 1.2j])
+    c = np.array([0.5 - 0.2j, -0.3 + 0.7j, 0.25 + 0.1j])
+    ctx.set_contour(z, c, 0.3 + 0.4j)
+    b = S.gaussian_spinor(dims, 1502, n=2)
+    got, st = sgn_gpu(ctx, b, tol=1e-12, mode=mode)
+    want, _, _ = cimpl.sign_apply_many(U, b, z, c, 0.3 + 0.4j, M0, tol=1e-13)
+    assert max(rel_per_source(got, want)) < PARITY
