@@ -523,10 +523,13 @@ __device__ __forceinline__ Cx<DF> proj_add<DF>(Cx<DF> a, Cx<DF> b) {
 //   A_mu (l0, l1) = (i^qa0 l_{swap}, i^qa1 l_{1-swap}):  A_x = -i sigma_1 (swap, -i, -i),
 //   A_y = -i sigma_2 (swap, -1, +1), A_z = -i sigma_3 (-i, +i), A_t = 1;
 //   A_mu^dag is the transpose with conjugate phases.
+// RAW (links carrying the boundary sign, !SIGNED): the partials hold the raw hop sums
+// and differences and phase 2 applies the direction's phases (compile-time there).
 template <typename R, bool CG, bool SIGNED = true>
 __device__ __forceinline__ void hw_split_phase1_compact(const typename Store<R>::T* __restrict__ in,
                                                         const typename Store<R>::T* __restrict__ U, const Geom& g,
                                                         int site0, Cx<R>* sm) {
+  constexpr bool RAW = !SIGNED;
   const int lane = threadIdx.x & 31, mu = threadIdx.x >> 5;
   const int s = site0 + lane;
   const int V = g.V;
@@ -573,9 +576,25 @@ __device__ __forceinline__ void hw_split_phase1_compact(const typename Store<R>:
       }
       Cx<R> u0, u1;
       hop.products(l, u0, u1);
+      Cx<R>* a = acc + i * kSplitSites;
+      if (RAW) {
+        // raw hop sums and differences, no phases: the slots of spins 0, 1 receive
+        // u_f + u_b per spin of the half spinor, those of spins 2, 3 receive u_b - u_f;
+        // phase 2 applies A_mu^dag (a compile-time swap and phase per direction)
+        if (dir == 0) {
+          a[0 * 3 * kSplitSites] = u0;
+          a[1 * 3 * kSplitSites] = u1;
+        } else {
+          const Cx<R> f0 = a[0 * 3 * kSplitSites], f1 = a[1 * 3 * kSplitSites];
+          a[0 * 3 * kSplitSites] = proj_add(f0, u0);
+          a[1 * 3 * kSplitSites] = proj_add(f1, u1);
+          a[2 * 3 * kSplitSites] = proj_add(u0, cneg(f0));
+          a[3 * 3 * kSplitSites] = proj_add(u1, cneg(f1));
+        }
+        continue;
+      }
       const Cx<R> c0 = uphase(u0, qs), c1 = uphase(u1, qs);
       const Cx<R> c2 = uphase(swap ? u1 : u0, qb0 + qd + qs), c3 = uphase(swap ? u0 : u1, qb1 + qd + qs);
-      Cx<R>* a = acc + i * kSplitSites;
       if (dir == 0) {  // the first hop initialises the partials
         a[0 * 3 * kSplitSites] = c0;
         a[1 * 3 * kSplitSites] = c1;
@@ -670,15 +689,42 @@ __device__ __forceinline__ bool hw_split_phase2(const typename Store<R>::T* __re
     }
     Cx<R> v;
     if constexpr (std::is_same<R, DF>::value) {
-      // diag x - 1/2 (p0 + p1 + p2 + p3) as one double-float sum of five terms: an
+      // diag x + the four direction partials as one double-float sum of five terms: an
       // error-free two-sum chain of the leading parts, the low parts and errors in one
       // float, one renormalisation (instead of four double-float additions)
       const Cx<R> dv = cscale(diag, x);
-      const Cx<R>* pp = sm + k * kSplitSites + lane;
-      v = {df_sum5<!HALVED>(dv.re, pp[0].re, pp[12 * kSplitSites].re, pp[24 * kSplitSites].re,
-                            pp[36 * kSplitSites].re),
-           df_sum5<!HALVED>(dv.im, pp[0].im, pp[12 * kSplitSites].im, pp[24 * kSplitSites].im,
-                            pp[36 * kSplitSites].im)};
+      if constexpr (HALVED) {
+        // raw partials (links carry -1/2 and the boundary sign): spins 0, 1 take the hop
+        // sums as stored; spins 2, 3 take A_mu^dag of the differences, a fixed swap and
+        // phase per direction
+        const int i = k - 3 * grp;
+        Cx<R> t[4];
+        if (grp < 2) {
+#pragma unroll
+          for (int m = 0; m < 4; ++m) t[m] = sm[(m * 12 + k) * kSplitSites + lane];
+        } else {
+          // spin 2 of direction mu is i^{q2[mu]} d_{s2[mu]}, spin 3 is i^{q3[mu]} d_{s3[mu]},
+          // d_s in slot 2 + s (A_x^dag = (i d1, i d0), A_y^dag = (d1, -d0),
+          // A_z^dag = (i d0, -i d1), A_t^dag = (d0, d1))
+          const bool sp2 = grp == 2;
+          const Cx<R> d0x = sm[(0 * 12 + (sp2 ? 9 : 6) + i) * kSplitSites + lane];
+          const Cx<R> d1y = sm[(1 * 12 + (sp2 ? 9 : 6) + i) * kSplitSites + lane];
+          const Cx<R> d2z = sm[(2 * 12 + (sp2 ? 6 : 9) + i) * kSplitSites + lane];
+          const Cx<R> d3t = sm[(3 * 12 + (sp2 ? 6 : 9) + i) * kSplitSites + lane];
+          t[0] = cmuli(d0x);                       // x: i d1 (spin 2), i d0 (spin 3)
+          t[1] = sp2 ? d1y : cneg(d1y);            // y: d1, -d0
+          t[2] = sp2 ? cmuli(d2z) : cmulmi(d2z);   // z: i d0, -i d1
+          t[3] = d3t;                              // t: d0, d1
+        }
+        v = {df_sum5<false>(dv.re, t[0].re, t[1].re, t[2].re, t[3].re),
+             df_sum5<false>(dv.im, t[0].im, t[1].im, t[2].im, t[3].im)};
+      } else {
+        const Cx<R>* pp = sm + k * kSplitSites + lane;
+        v = {df_sum5<true>(dv.re, pp[0].re, pp[12 * kSplitSites].re, pp[24 * kSplitSites].re,
+                           pp[36 * kSplitSites].re),
+             df_sum5<true>(dv.im, pp[0].im, pp[12 * kSplitSites].im, pp[24 * kSplitSites].im,
+                           pp[36 * kSplitSites].im)};
+      }
     } else if constexpr (HALVED) {
       v = {fma(diag, x.re, t.re), fma(diag, x.im, t.im)};
     } else {
