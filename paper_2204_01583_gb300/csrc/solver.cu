@@ -47,10 +47,11 @@ namespace {
 constexpr int NT1 = 128;  // K1: stencil + Lanczos epilogue; K3: regeneration pass
 constexpr int NT2 = 256;  // K2: vector updates
 // Resident blocks per SM the stencil kernels are compiled for: 4 (<= 128 registers) for
-// FP64; 8 (<= 64 registers) for double-float, whose stencil gains from
-// the extra warps (16^3x32, 12 sources: 766 / 744 / 734 us per launch at 6 / 7 / 8).
+// FP64; 7 (<= 72 registers) for double-float (16^3x32, 12 sources, double-float solve:
+// 467 / 421 / 457 ms at 6 / 7 / 8 blocks per SM -- at 8 the 64-register limit spills
+// and the shared-memory partials leave L1 almost no room).
 template <typename R>
-constexpr int k1_min_blocks() { return std::is_same<R, DF>::value ? 8 : 4; }
+constexpr int k1_min_blocks() { return std::is_same<R, DF>::value ? 7 : 4; }
 // FP64 and double-float solves read the link copy scaled by -1/2 (the hop factor of D_W) with the time
 // boundary sign on the last time slice's time links, so phase 1 applies no boundary sign
 // and phase 2 adds the partials to the diagonal term without a multiplication
