@@ -531,9 +531,10 @@ def run_ours(args, wl):
 
 
 # Algorithmic work per unit for each kernel class (FP64): (flops, bytes).
-# Units: "si" = source-iteration x site, "nu" = node-update x site.
-#   lanczos_hw_kernel:     H_W stencil 1368 flop + epilogue 72 flop; links 576 B + U_i, U_{i-1}
-#                          read and w written (3 x 192 B)                      per si
+# Units: "si" = source-iteration x site, "nu" = node-update x site, "ls" = launch x site.
+#   lanczos_hw_kernel:     H_W stencil 1368 flop + epilogue 72 flop; U_i, U_{i-1} read and
+#                          w written (3 x 192 B)                               per si
+#                          + the links, 576 B, once for all sources of a launch   per ls
 #   lanczos_update_kernel: U_{i+1} = w - alpha v (12 x 10 flop; 3 x 192 B)    per si
 #                          + p = v - l p and s += c zeta p (12 x 16 flop; p read+write 384 B) per nu
 #   lanczos_regen_kernel:  stencil + Lanczos update + s += g v (1368 + 12 x 24 flop;
@@ -544,7 +545,7 @@ def run_ours(args, wl):
 FP64_WORK = {
     "basis_sum_kernel": {"si": (96.0, 192.0)},
     "lanczos_coop_kernel": {"si": (1560.0, 1728.0)},
-    "lanczos_hw_kernel": {"si": (1440.0, 1152.0)},
+    "lanczos_hw_kernel": {"si": (1440.0, 576.0), "ls": (0.0, 576.0)},
     "lanczos_update_kernel": {"si": (120.0, 576.0), "nu": (192.0, 384.0)},
     "lanczos_regen_kernel": {"si": (1656.0, 1728.0)},
 }
@@ -615,8 +616,9 @@ def roofline(wl, mode, ktimes, kstats, nsrc):
             continue
         d = {"launches": n, "ms": ms, "avg_us": ms / n * 1e3}
         if mode in ("fp64", "fp64_2pass", "fp64_regen", "f32x2") and k in FP64_WORK:
-            fl = sum(units[u] * w[0] for u, w in FP64_WORK[k].items())
-            by = sum(units[u] * w[1] for u, w in FP64_WORK[k].items())
+            uk = dict(units, ls=n * V)
+            fl = sum(uk[u] * w[0] for u, w in FP64_WORK[k].items())
+            by = sum(uk[u] * w[1] for u, w in FP64_WORK[k].items())
             d["tflops"] = fl / (ms / 1e3) / 1e12
             d["gbs"] = by / (ms / 1e3) / 1e9
         out[k] = d
