@@ -1320,9 +1320,10 @@ int setup_ws(ov_ctx* ctx, int nsrc, int ns, bool want_x, bool want_sacc, bool wa
 // K1's grid for n sources: one dimension, the n sources of a site tile in consecutive
 // blocks, so that they run side by side and the tile's links come from DRAM once for
 // all of them (L2 serves the rest).  With the sources in a second grid dimension each
-// source swept the whole lattice in turn and re-read the link field from DRAM: 445 vs
-// 425 ms for the 12-source double-float solve at 16^3 x 32 (the FP64 stencil, bound by
-// its FP64 pipe, runs the same either way).
+// source swept the whole lattice in turn and re-read the link field from DRAM (16^3 x
+// 32, 6 sources: 522 MB of DRAM traffic per launch here, about 850 MB that way).  The
+// time hardly moves, since neither stencil is DRAM-bound: FP64 1386 ms per 12-source
+// solve either way, double-float 424.4 vs 421.7 ms.
 template <typename R>
 dim3 k1_grid(const SolveWs<R>& w, int n) {
   return dim3((unsigned)w.nblk1 * (unsigned)n);
