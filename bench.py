@@ -476,11 +476,15 @@ def run_ours(args, wl):
         ho_opts = ctx.opts(mode=mode, tol=wl["tol"], host_io=True, max_iter=max_iter)
         step(ho_opts, hb, ho, stream)
         barrier()
+        esampler = ClockSampler(local)
+        esampler.start()
         te, _ = timed_steps(lambda: step(ho_opts, hb, ho, stream), args.steps, stream, flush)
         barrier()
+        eclocks = esampler.stop()
         tot = max_over_ranks(sum(te))
         nbytes = int(b.nbytes)
-        e2e = {"value": applies / (tot / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+        e2e = {"value": applies / (tot / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "ms_per_step": tot / args.steps, "clocks": eclocks}
 
     # per-kernel durations (library events on the launching stream), a few more steps
     ctx.set_kernel_timing(True)

@@ -107,11 +107,15 @@ def test_two_pass_equals_shifted(gpu_lib, config2, mode):
     assert sc["node_updates"] == 0 and sa["node_updates"] > 0
 
 
+@pytest.mark.parametrize("groups", [0, 1], ids=["auto-groups", "one-launch"])
 @pytest.mark.parametrize("mode", ["fp64", "fp64_2pass", "fp64_regen", "f32x2"])
-def test_ragged_lattice_parity(gpu_lib, mode):
-    """Lattice whose volume is not a multiple of any block size; 3 sources."""
+def test_ragged_lattice_parity(gpu_lib, mode, groups):
+    """Lattice whose volume is not a multiple of any block size; 3 sources, either one
+    graph branch per source or all three in each launch (the stencil grid then holds the
+    three sources of every 32-site tile side by side, the last tile ragged)."""
     dims = (3, 5, 4, 6)
     ctx, U = make_ctx(gpu_lib, dims, 0.5, 51)
+    ctx.set_concurrency(groups)
     ctx.set_contour_ellipse(24, 3.4, 3.4, 0.3)
     b = S.gaussian_spinor(dims, 52, n=3)
     got, st = sgn_gpu(ctx, b, tol=1e-12, mode=mode)
