@@ -478,13 +478,13 @@ def run_ours(args, wl):
         barrier()
         esampler = ClockSampler(local)
         esampler.start()
-        te, _ = timed_steps(lambda: step(ho_opts, hb, ho, stream), args.steps, stream, flush)
+        te, est = timed_steps(lambda: step(ho_opts, hb, ho, stream), args.steps, stream, flush)
         barrier()
         eclocks = esampler.stop()
         tot = max_over_ranks(sum(te))
         nbytes = int(b.nbytes)
         e2e = {"value": applies / (tot / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-               "ms_per_step": tot / args.steps, "clocks": eclocks}
+               "ms_per_step": tot / args.steps, "clocks": eclocks, "launches_per_step": est[-1]["launches"]}
 
     # per-kernel durations (library events on the launching stream), a few more steps
     ctx.set_kernel_timing(True)
@@ -506,7 +506,7 @@ def run_ours(args, wl):
         "gpu_launches": int(sum(s["launches"] for s in stats)), "roofline": roof, "kernels": kernels,
         "solver": {"iterations": stats[-1]["iterations"], "max_residual": stats[-1]["max_residual"],
                    "error_bound": stats[-1]["error_bound"], "converged": stats[-1]["converged"],
-                   "lanczos_spectrum": spec},
+                   "launches_per_step": stats[-1]["launches"], "lanczos_spectrum": spec},
     }
     if not capped and not nodes_split and args.compare_steps > 0:
         for other in wl.get("compare", ()):

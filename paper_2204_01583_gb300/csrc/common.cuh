@@ -551,6 +551,17 @@ __device__ __forceinline__ void hw_split_phase1_compact(const typename Store<R>:
     const int sl = dir == 0 ? s : sn;  // link site
     const int qd = dir == 0 ? 2 : 0;   // forward hop: h = psi_up - A psi_lo, lower gets -A^dag u
     const int qs = sgn < 0 ? 2 : 0;    // boundary sign
+    // link rows are loaded one row ahead of their use (row 0 together with the spinor),
+    // so that each load's latency is covered by the previous row's products; the
+    // conjugation of the backward hop is applied when a row is taken into use
+    const typename Store<R>::T* Ul = U + (size_t)mu * 9 * V + sl;
+    // forward: U[i][j]; backward: (U^dag)[i][j] = conj(U[j][i])
+    auto ld_row = [&](int i, Cx<R> l[3]) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) l[j] = ld<R>(Ul + (dir == 0 ? (i * 3 + j) : (j * 3 + i)) * (size_t)V);
+    };
+    Cx<R> ln[3];
+    ld_row(0, ln);
     Cx<R> h0[3], h1[3];
 #pragma unroll
     for (int col = 0; col < 3; ++col) {
@@ -563,17 +574,12 @@ __device__ __forceinline__ void hw_split_phase1_compact(const typename Store<R>:
     }
     RowOperand<R> hop;
     hop.set(h0, h1);
-    const typename Store<R>::T* Ul = U + (size_t)mu * 9 * V + sl;
 #pragma unroll 1
     for (int i = 0; i < 3; ++i) {
       Cx<R> l[3];
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        // forward: U[i][j]; backward: (U^dag)[i][j] = conj(U[j][i])
-        const int e = dir == 0 ? (i * 3 + j) : (j * 3 + i);
-        l[j] = ld<R>(Ul + e * (size_t)V);
-        if (dir) l[j].im = -l[j].im;
-      }
+      for (int j = 0; j < 3; ++j) l[j] = dir ? Cx<R>{ln[j].re, -ln[j].im} : ln[j];
+      if (i < 2) ld_row(i + 1, ln);
       Cx<R> u0, u1;
       hop.products(l, u0, u1);
       Cx<R>* a = acc + i * kSplitSites;
