@@ -484,7 +484,9 @@ def run_ours(args, wl):
         tot = max_over_ranks(sum(te))
         nbytes = int(b.nbytes)
         e2e = {"value": applies / (tot / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-               "ms_per_step": tot / args.steps, "clocks": eclocks, "launches_per_step": est[-1]["launches"]}
+               "ms_per_step": tot / args.steps, "clocks": eclocks, "launches_per_step": est[-1]["launches"],
+               "library_ms_per_step": sum(x["ms"] for x in est) / len(est),
+               "step_ms_min_median_max": [min(te), float(np.median(te)), max(te)]}
 
     # per-kernel durations (library events on the launching stream), a few more steps
     ctx.set_kernel_timing(True)
@@ -506,7 +508,10 @@ def run_ours(args, wl):
         "gpu_launches": int(sum(s["launches"] for s in stats)), "roofline": roof, "kernels": kernels,
         "solver": {"iterations": stats[-1]["iterations"], "max_residual": stats[-1]["max_residual"],
                    "error_bound": stats[-1]["error_bound"], "converged": stats[-1]["converged"],
-                   "launches_per_step": stats[-1]["launches"], "lanczos_spectrum": spec},
+                   "launches_per_step": stats[-1]["launches"],
+                   "library_ms_per_step": sum(x["ms"] for x in stats) / len(stats),
+                   "step_ms_min_median_max": [min(t_steps), float(np.median(t_steps)), max(t_steps)],
+                   "lanczos_spectrum": spec},
     }
     if not capped and not nodes_split and args.compare_steps > 0:
         for other in wl.get("compare", ()):

@@ -104,7 +104,8 @@ typedef struct {
   double tol;       /* per-node relative residual ||b - (z_j - H) y_j|| / ||b||   [1e-12] */
   int max_iter;     /* Krylov iteration limit per solve                          [20000] */
   int host_io;      /* 1: b / out / eta / grad_b are HOST pointers; copies to and
-                       from the device are enqueued on `stream` inside the call  [0] */
+                       from the device are enqueued on `stream` inside the call
+                       (page-locked inputs are read by a kernel, others copied)  [0] */
   int check_every;  /* iterations between host reads of the convergence flag  [32] */
   int use_graph;    /* 1: replay the per-iteration kernels from a CUDA graph     [1] */
   int node_chunk;   /* VJP: nodes whose forward and adjoint solutions are held at once;

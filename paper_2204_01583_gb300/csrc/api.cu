@@ -3,6 +3,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -155,15 +156,67 @@ double now_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+namespace {
+__global__ void copy16_kernel(const double2* __restrict__ src, double2* __restrict__ dst, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    dst[t] = src[t];
+}
+
+// The device address of page-locked host memory (cudaHostAlloc, cudaHostRegister), or null
+// for any other pointer.
+const void* pinned_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // an unknown pointer: a non-sticky error, left to the copy below
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+}  // namespace
+
 // Device copy of a (possibly host) canonical spinor set; returns the device pointer.
+// Page-locked host memory is read by a kernel over the host link: on GB300 the copy
+// engine's host-to-device rate for a 302 MB set fell from ~210 GB/s to 15-60 GB/s in the
+// course of repeated long solves, while a kernel reading the same buffer stayed at
+// ~215 GB/s.  Other host memory goes through cudaMemcpyAsync.
 const double2* stage_in(ov_ctx* ctx, const void* p, size_t bytes, int host_io, const char* name, cudaStream_t s,
                         int* st) {
   if (!host_io) return (const double2*)p;
   void* d = ws_get(ctx, name, bytes, st);
   if (*st != OV_OK) return nullptr;
+  const void* hp = pinned_device_ptr(p);
+  if (hp && ((uintptr_t)hp & 15) == 0 && bytes % 16 == 0) {
+    const size_t n = bytes / 16;
+    const unsigned grid = (unsigned)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 8));
+    cudaEvent_t ev;
+    kt_begin(ctx, KC_LAYOUT, s, &ev);
+    copy16_kernel<<<grid, 256, 0, s>>>((const double2*)hp, (double2*)d, n);
+    kt_end(ctx, KC_LAYOUT, s, ev);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) *st = ctx_cuda(ctx, e, "copy16_kernel");
+    return (const double2*)d;
+  }
   cudaError_t e = cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) *st = ctx_cuda(ctx, e, "host-to-device copy");
   return (const double2*)d;
+}
+
+// Copy of a device result to host memory: written by a kernel when the destination is
+// page-locked (as stage_in reads), else by cudaMemcpyAsync.
+int stage_out(ov_ctx* ctx, void* host, const void* dev, size_t bytes, cudaStream_t s) {
+  void* hp = const_cast<void*>(pinned_device_ptr(host));
+  if (hp && ((uintptr_t)hp & 15) == 0 && ((uintptr_t)dev & 15) == 0 && bytes % 16 == 0) {
+    const size_t n = bytes / 16;
+    const unsigned grid = (unsigned)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 8));
+    cudaEvent_t ev;
+    kt_begin(ctx, KC_LAYOUT, s, &ev);
+    copy16_kernel<<<grid, 256, 0, s>>>((const double2*)dev, (double2*)hp, n);
+    kt_end(ctx, KC_LAYOUT, s, ev);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? OV_OK : ctx_cuda(ctx, e, "copy16_kernel");
+  }
+  const cudaError_t e = cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, s);
+  return e == cudaSuccess ? OV_OK : ctx_cuda(ctx, e, "device-to-host copy");
 }
 
 namespace {
@@ -661,9 +714,8 @@ static int sign_or_overlap(ov_ctx* ctx, bool overlap, double m_q, const void* b,
     st = launch_unpack64(ctx, s_soa, od, nrhs, s);
   if (st != OV_OK) return st;
   if (o.host_io) {
-    cudaError_t e = cudaMemcpyAsync(out, od, sizeof(double2) * n, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return ctx_cuda(ctx, e, "device-to-host copy");
-    e = cudaStreamSynchronize(s);
+    if ((st = stage_out(ctx, out, od, sizeof(double2) * n, s)) != OV_OK) return st;
+    const cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return ctx_cuda(ctx, e, "sync");
   }
   kt_collect(ctx);
@@ -815,11 +867,15 @@ int vjp_core(ov_ctx* ctx, double a_eta, double gsc, double fsc, bool gamma5_eta,
   if (grad_b) {
     double2* dst = o.host_io ? gbo : (double2*)grad_b;
     if ((st = launch_unpack64(ctx, gb, dst, 1, s))) return st;
-    if (o.host_io) e = cudaMemcpyAsync(grad_b, gbo, sizeof(double2) * n12, cudaMemcpyDeviceToHost, s);
+    if (o.host_io && (st = stage_out(ctx, grad_b, gbo, sizeof(double2) * n12, s)) != OV_OK) return st;
   }
-  if (e == cudaSuccess && grad_links)
-    e = cudaMemcpyAsync(grad_links, F, sizeof(double) * 32 * (size_t)V,
-                        o.host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s);
+  if (grad_links) {
+    if (o.host_io) {
+      if ((st = stage_out(ctx, grad_links, F, sizeof(double) * 32 * (size_t)V, s)) != OV_OK) return st;
+    } else {
+      e = cudaMemcpyAsync(grad_links, F, sizeof(double) * 32 * (size_t)V, cudaMemcpyDeviceToDevice, s);
+    }
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return ctx_cuda(ctx, e, "VJP outputs");
   kt_collect(ctx);

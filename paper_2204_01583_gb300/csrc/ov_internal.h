@@ -216,6 +216,7 @@ int check_opts(ov_ctx* ctx, const ov_solve_opts& o);
 double now_ms();
 const double2* stage_in(ov_ctx* ctx, const void* p, size_t bytes, int host_io, const char* name, cudaStream_t s,
                         int* st);
+int stage_out(ov_ctx* ctx, void* host, const void* dev, size_t bytes, cudaStream_t s);
 int sign_core(ov_ctx* ctx, const double2* b_dev, int nrhs, const ov_solve_opts& o, SolveOut* so, cudaStream_t s,
               double2** s_soa_out, double2* xs);
 void fill_stats(ov_stats* st, const SolveOut& so, double ms);

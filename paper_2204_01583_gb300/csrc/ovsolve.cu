@@ -257,8 +257,8 @@ extern "C" int ov_overlap_solve(ov_ctx* ctx, double m_q, const void* b, void* x,
     if (rr0[k] > 0.0) worst_ne = std::max(worst_ne, std::sqrt(rr[k] / rr0[k]));
   }
   if (host_io) {
-    e = cudaMemcpyAsync(x, xd, bytes, cudaMemcpyDeviceToHost, c.s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c.s);
+    if ((st = stage_out(ctx, x, xd, bytes, c.s)) != OV_OK) return st;
+    e = cudaStreamSynchronize(c.s);
     if (e != cudaSuccess) return ctx_cuda(ctx, e, "device-to-host copy");
   }
   SolveOut so = c.acc;

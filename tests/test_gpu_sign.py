@@ -162,14 +162,27 @@ def test_overlap_epilogue(gpu_lib):
 
 
 def test_host_io_matches_device_io(gpu_lib):
+    """Host buffers, pageable (copied by the copy engine) and page-locked (read by a
+    kernel), give the device-buffer result bit for bit, for the sign and the overlap."""
+    import torch
+
     dims = (4, 4, 4, 4)
     ctx, U = make_ctx(gpu_lib, dims, 0.3, 91)
     ctx.set_contour_ellipse(32, 3.4, 3.4, 0.3)
-    b = S.gaussian_spinor(dims, 92)
-    dev, _ = sgn_gpu(ctx, b)
+    b = S.gaussian_spinor(dims, 92, n=2)
+    dev, _ = sgn_gpu(ctx, b, nrhs=2)
     out = np.empty_like(b)
-    ctx.sgn(b, out, 1, ctx.opts(host_io=True))
+    ctx.sgn(b, out, 2, ctx.opts(host_io=True))
     assert np.array_equal(out, dev)
+    hb = torch.from_numpy(b).pin_memory()
+    ho = torch.empty_like(hb).pin_memory()
+    ctx.sgn(hb, ho, 2, ctx.opts(host_io=True))
+    assert np.array_equal(ho.numpy(), dev)
+    bd = to_dev(b)
+    od = torch.empty_like(bd)
+    ctx.overlap(0.1, bd, od, 2, ctx.opts())
+    ctx.overlap(0.1, hb, ho, 2, ctx.opts(host_io=True))
+    assert np.array_equal(ho.numpy(), to_host(od))
 
 
 def test_graph_and_direct_launch_agree_bitwise(gpu_lib):

@@ -151,3 +151,25 @@ def test_coefficient_space_vjp_matches_vector_space(gpu_lib, config4, mode, chun
     gb2, F2, st2 = _vjp(gpu_lib, ctx, eta, b, mode=mode, node_chunk=chunk)
     assert rel(gb2, gb) < 1e-10
     assert np.abs(F2 - F).max() <= 1e-10 * np.abs(F).max()
+
+
+def test_host_buffers_give_the_device_result(gpu_lib):
+    """ov_sgn_vjp with host_io: pageable numpy buffers (copy engine) and page-locked torch
+    buffers (read and written by kernels) give the device-buffer gradients bit for bit."""
+    import torch
+
+    dims = (4, 4, 4, 4)
+    ctx, U = make_ctx(gpu_lib, dims, 0.3, 621)
+    ctx.set_contour_ellipse(24, 3.3, 3.3, 0.3)
+    b = S.gaussian_spinor(dims, 622)
+    eta = S.gaussian_spinor(dims, 623)
+    gb, F, _ = _vjp(gpu_lib, ctx, eta, b)
+    for pinned in (False, True):
+        hb, he = torch.from_numpy(b.copy()), torch.from_numpy(eta.copy())
+        hg = torch.empty_like(hb)
+        hF = torch.empty((4,) + b.shape[:4] + (8,), dtype=torch.float64)
+        if pinned:
+            hb, he, hg, hF = hb.pin_memory(), he.pin_memory(), hg.pin_memory(), hF.pin_memory()
+        ctx.sgn_vjp(he, hb, hg, hF, ctx.opts(tol=1e-13, host_io=True))
+        assert np.array_equal(hg.numpy(), gb), pinned
+        assert np.array_equal(hF.numpy(), F), pinned
