@@ -325,9 +325,8 @@ int ov_kernel_times(ov_ctx* ctx, const char** names, long long* launches, double
  * 576 V + 384 V nrhs bytes (V = sites, each part rounded up to 256 B) and larger
  * requests return OV_ERR_SCRATCH_TOO_SMALL.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress, with that device current) and
- * keeps it for the life of the process; make that first call before any stream
- * capture, and do not use the entry point on a device after cudaDeviceReset (the
- * kept address belongs to the old context).  Every call on a device shares the one
+ * keeps it for the life of the process; do not use the entry point on a device after
+ * cudaDeviceReset (the kept address belongs to the old context).  Every call on a device shares the one
  * array: calls that overlap on the GPU (different streams, or different host
  * threads) race and must be serialised by the caller.  Nothing in the array needs to
  * start at zero: each call writes all it reads.  Errors: INVALID_ARG (null or
