@@ -185,39 +185,33 @@ __device__ __forceinline__ void hop_pair12(const float4* __restrict__ in, const 
     const float2 nfl = dir == 0 ? f2(-f, -f) : f2(f, f);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      float2 a0 = f2(0.f, 0.f), b0 = f2(0.f, 0.f), c0 = f2(0.f, 0.f);
-      float2 a1 = f2(0.f, 0.f), b1 = f2(0.f, 0.f), c1 = f2(0.f, 0.f);
+      float2 a0 = f2(0.f, 0.f), c0 = f2(0.f, 0.f);
+      float2 a1 = f2(0.f, 0.f), c1 = f2(0.f, 0.f);
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         // row 2 is rebuilt element by element where it is used
         const int r = dir == 0 ? i : j, q = dir == 0 ? j : i;
         const B2 l = (r < 2 || LK >= 2) ? U[r][q] : link12_row2(U, q);
+        const float2 nli = f2(-l.im.x, -l.im.y);
         a0 = fma2(l.re, h0[j].re, a0);
         a1 = fma2(l.re, h1[j].re, a1);
         c0 = fma2(l.re, h0[j].im, c0);
         c1 = fma2(l.re, h1[j].im, c1);
         if (dir == 0) {
-          // U h: re = lr hr - li hi, im = lr hi + li hr
-          b0 = fma2(l.im, h0[j].im, b0);
-          b1 = fma2(l.im, h1[j].im, b1);
+          // U h: re = lr hr - li hi, im = lr hi + li hr (the minus in the operand)
+          a0 = fma2(nli, h0[j].im, a0);
+          a1 = fma2(nli, h1[j].im, a1);
           c0 = fma2(l.im, h0[j].re, c0);
           c1 = fma2(l.im, h1[j].re, c1);
         } else {
           // U^dag h: re = lr hr + li hi, im = lr hi - li hr
           a0 = fma2(l.im, h0[j].im, a0);
           a1 = fma2(l.im, h1[j].im, a1);
-          b0 = fma2(l.im, h0[j].re, b0);
-          b1 = fma2(l.im, h1[j].re, b1);
+          c0 = fma2(nli, h0[j].re, c0);
+          c1 = fma2(nli, h1[j].re, c1);
         }
       }
-      P2 u0, u1;
-      if (dir == 0) {
-        u0 = {sub2(a0, b0), c0};
-        u1 = {sub2(a1, b1), c1};
-      } else {
-        u0 = {a0, sub2(c0, b0)};
-        u1 = {a1, sub2(c1, b1)};
-      }
+      const P2 u0 = {a0, c0}, u1 = {a1, c1};
       acc[0 * 3 + i].re = fma2(fu, u0.re, acc[0 * 3 + i].re);
       acc[0 * 3 + i].im = fma2(fu, u0.im, acc[0 * 3 + i].im);
       acc[1 * 3 + i].re = fma2(fu, u1.re, acc[1 * 3 + i].re);
