@@ -1270,6 +1270,9 @@ int setup_ws(ov_ctx* ctx, int nsrc, int ns, bool want_x, bool want_sacc, bool wa
   int st = OV_OK;
   std::string t(tag);
   w->nblk1 = (V + kSplitSites - 1) / kSplitSites;
+  // K1's one-dimensional grid holds every (tile, source) pair of a launch
+  if ((size_t)w->nblk1 * (size_t)nsrc > (size_t)0x7fffffff)
+    return ctx_fail(ctx, OV_ERR_INVALID_ARG, "too many sources for one stencil launch at this volume");
   w->nshift = ns;
   w->max_iter = max_iter;
   // the init kernel uses the K2 partial buffer with up to ceil(12V / NT2) blocks
