@@ -49,7 +49,8 @@ constexpr int NT2 = 256;  // K2: vector updates
 // Resident blocks per SM the stencil kernels are compiled for: 4 (<= 128 registers) for
 // FP64; 7 (<= 72 registers) for double-float (16^3x32, 12 sources, double-float solve:
 // 467 / 421 / 457 ms at 6 / 7 / 8 blocks per SM -- at 8 the 64-register limit spills
-// and the shared-memory partials leave L1 almost no room).
+// and the shared-memory partials leave L1 almost no room; with the link rows loaded one
+// row ahead, 414 / 407.5 ms at 6 / 7).
 template <typename R>
 constexpr int k1_min_blocks() { return std::is_same<R, DF>::value ? 7 : 4; }
 // FP64 and double-float solves read the link copy scaled by -1/2 (the hop factor of D_W) with the time
