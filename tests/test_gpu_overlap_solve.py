@@ -92,3 +92,7 @@ def test_overlap_solve_edge_cases(gpu_lib):
     xd2 = torch.empty_like(bd)
     ctx.overlap_solve(0.2, bd, xd2, 1, ctx.opts(tol=1e-13), tol=1e-12)
     assert np.array_equal(hx.numpy(), to_host(xd2))
+    # page-locked host buffers (read and written by kernels, not the copy engine)
+    pb, px = hb.pin_memory(), torch.empty_like(hb).pin_memory()
+    ctx.overlap_solve(0.2, pb, px, 1, ctx.opts(tol=1e-13, host_io=True), tol=1e-12)
+    assert np.array_equal(px.numpy(), to_host(xd2))
