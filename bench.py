@@ -707,10 +707,9 @@ def run_dslash(args, wl):
         torch.cuda.synchronize()
         n, ms = ctx.kernel_times()["hw_kernel"]
         ctx.set_kernel_timing(False)
-        # algorithmic link reals: 72 for the forms that read all 9 elements (plain,
-        # broadcast, padded pairs), 48 for the 12-real forms; duplicated lanes and padding
-        # are not counted
-        link_reals = 48 if comp in (1, 4, 7, 8, 9, 12) else 72
+        # algorithmic link reals: 72 for the plain links (all 9 elements), 48 for the
+        # 12-real forms; duplicated lanes are not counted
+        link_reals = 48 if comp in (1, 8, 9, 12) else 72
         by = V * (link_reals * s_real + nrhs * 48 * s_real)  # links once per launch; each RHS in + out
         per = ms / n / 1e3
         rows.append({"variant": k, "rhs_tile": rt, "compressed_links": bool(comp), "threads": nt,
@@ -720,8 +719,7 @@ def run_dslash(args, wl):
     best = min(rows, key=lambda r: r["us"])  # the variant the autotuner keeps
     if fp32:
         code = variants[[r["variant"] for r in rows].index(best["variant"])][1][1]
-        kern = {0: "hw32_tile_kernel", 1: "hw32_tile_kernel", 4: "hw32_s4_kernel",
-                8: "hw32_s4_kernel"}.get(code, "hw_pair12_kernel")
+        kern = {0: "hw32_tile_kernel", 1: "hw32_tile_kernel", 8: "hw32_s4_kernel"}.get(code, "hw_pair12_kernel")
         if code in (0, 1) and best["rhs_tile"] == 0:
             kern = "hw32_split_kernel"
     else:

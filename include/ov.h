@@ -269,23 +269,21 @@ int ov_overlap_vjp(ov_ctx* ctx, double m_q, const void* eta, const void* b, void
 int ov_overlap_solve(ov_ctx* ctx, double m_q, const void* b, void* x, int nrhs, const ov_solve_opts* inner,
                      double tol, int max_iter, ov_stats* stats, void* stream);
 
-/* FP32 stencil selection for ov_apply_HW(OV_FP32) and the FP32 phases of the mixed
- * solve (implementation choices of the H_W stencil of Eq. 1; the paper has no
- * counterpart).  Variants differ in right-hand sides per thread (link loads reused across
- * them), 12-real link compression (row 2 rebuilt as conj(row0 x row1)) and block
- * size.  k = -1 (default): autotune -- each variant is timed once on the live data per
- * right-hand-side count and the fastest is kept.  ov_hw32_variants returns the number
- * of variants and, for 0 <= k < count, describes variant k.  compressed: 0 plain
- * links, 1 12-real links (structure-of-arrays float2 layout, the layout the mixed solve
- * uses); 4: spin-paired float4 layout (one 16-byte load per spin pair) with 12-real
- * links; 7: right-hand-side-paired layout (one float4 holds a component of two RHS,
- * paired FP32 instructions act on both) with compact 12-real links (48 B per link, lanes
- * broadcast in registers); 8 and 9: the spin-paired (8) and paired (9) 12-real kernels
- * reading the diagonal term before the hops, with 128 or 256 threads; 10: code 9
- * (128 threads) reading all 9 link elements (80 B per link with padding; no rebuild);
- * 12: code 9 (128 threads) with row 2 rebuilt once in scalar arithmetic (both lanes of
- * a pair need the same value).  rhs_tile 0: four threads per site (one per direction),
- * partial sums combined in shared memory. */
+/* FP32 stencil selection for ov_apply_HW(OV_FP32) (implementation choices of the H_W
+ * stencil of Eq. 1; the paper has no counterpart).  Variants differ in layout, right-hand
+ * sides per thread (link loads reused across them) and 12-real link compression (row 2
+ * rebuilt as conj(row0 x row1)).  k = -1 (default): autotune -- each variant is timed
+ * once on the live data per right-hand-side count and the fastest is kept.
+ * ov_hw32_variants returns the number of variants and, for 0 <= k < count, describes
+ * variant k.  Structure-of-arrays float2 layout: compressed 0 plain links, 1 12-real
+ * links; rhs_tile = right-hand sides per thread, 0 = four threads per site (one per
+ * direction, partial sums combined in shared memory).  compressed 8: spin-paired float4
+ * layout (one 16-byte load per spin pair), one RHS per thread, 12-real links;
+ * 9: right-hand-side-paired float4 layout (one float4 holds a component of two RHS,
+ * paired FP32 instructions act on both) with compact 12-real links (48 B per link,
+ * lanes broadcast in registers); 12: code 9 with row 2 rebuilt once in scalar
+ * arithmetic (both lanes of a pair need the same value).  All read the diagonal term
+ * before the hops, 128 threads per block except rhs_tile 0. */
 int ov_set_hw32_variant(ov_ctx* ctx, int k);
 int ov_hw32_variants(int k, int* rhs_tile, int* compressed, int* threads);
 

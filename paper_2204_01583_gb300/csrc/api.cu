@@ -385,17 +385,12 @@ int ov_set_gauge(ov_ctx* ctx, const double* U, int on_device, void* stream) {
 // float4 per site and RHS; its buffers alias the paired ones, 6 <= 12 per pair).
 struct Float4Variant {
   bool paired;
-  int form;              // P: launch_hw_pair12 form; S: launch_hw32_s4 comp
+  int form;              // P: launch_hw_pair12 form; S: unused (one S kernel)
   int rhs_tile, code, threads;  // as reported by ov_hw32_variants
 };
 constexpr Float4Variant kFloat4Variants[] = {
-    {false, 1, 1, 4, 128},  // S, 12-real links
-    {true, 1, 2, 7, 128},   // P, 12-real links compact
-    {false, 3, 1, 8, 128},  // S, 12-real links, centre first
-    {false, 4, 1, 8, 256},  // S, 12-real links, centre first, 256 threads per block
+    {false, 0, 1, 8, 128},  // S, 12-real links, centre first
     {true, 2, 2, 9, 128},   // P, 12-real compact links, centre first
-    {true, 3, 2, 9, 256},   // P, the same with 256 threads per block
-    {true, 4, 2, 10, 128},  // P, all 9 link elements (padded 5 float4), centre first
     {true, 6, 2, 12, 128},  // P, 12-real compact links, centre first, row 2 rebuilt in scalar
 };
 constexpr int kNFloat4Variants = sizeof(kFloat4Variants) / sizeof(kFloat4Variants[0]);
@@ -412,7 +407,7 @@ static int fp32_float4_unpack(ov_ctx* ctx, int v, const float4* buf, float2* out
 static int fp32_float4_launch(ov_ctx* ctx, int v, const float4* in, float4* out, int nrhs, cudaStream_t s) {
   const Float4Variant& f = kFloat4Variants[v];
   const int npair = (nrhs + 1) / 2;
-  if (!f.paired) return launch_hw32_s4(ctx, in, out, nrhs, f.form, s);
+  if (!f.paired) return launch_hw32_s4(ctx, in, out, nrhs, s);
   return launch_hw_pair12(ctx, in, out, npair, f.form, s);
 }
 

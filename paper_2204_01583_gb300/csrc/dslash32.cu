@@ -184,11 +184,12 @@ struct Cand {
   LaunchFn fn;
 };
 
+// The structure-of-arrays variants kept: each is the fastest, or within 0.5% of it, for
+// some lattice and right-hand-side count of a sweep over 8^4, 12^3 x 24, 16^4 and
+// 16^3 x 32 with 1, 2, 3, 4, 6, 8 and 12 RHS (six others never were and were removed).
 const Cand kCands[] = {
-    {1, false, 128, launch_variant<1, false, 128>}, {1, true, 128, launch_variant<1, true, 128>},
-    {2, false, 128, launch_variant<2, false, 128>}, {2, true, 128, launch_variant<2, true, 128>},
-    {4, true, 128, launch_variant<4, true, 128>},   {4, true, 64, launch_variant<4, true, 64>},
-    {2, true, 256, launch_variant<2, true, 256>},   {1, true, 256, launch_variant<1, true, 256>},
+    {1, true, 128, launch_variant<1, true, 128>},
+    {2, false, 128, launch_variant<2, false, 128>},
     {0, false, kSplitNT, launch_split},  // rhs tile 0: four threads per site
 };
 constexpr int kNCands = sizeof(kCands) / sizeof(kCands[0]);
@@ -267,42 +268,29 @@ void hw32_variant_info(int k, int* rt, int* comp, int* nt) {
 // Spin-paired FP32 layout ("S4"): one float4 holds (psi[s][c], psi[s+2][c]) for an upper
 // spin s in {0, 1}; element (rhs r, pair p = 3 s + c, site) at (r * 6 + p) * V + site.
 // A neighbour spinor is 6 loads of 16 bytes (the float2 layout needs 12 of 8 bytes), and
-// the addressing is 32-bit.  Links: 5 float4 per (mu, site) holding the 9 elements of U
-// row-major in pairs (the 10th slot is padding), or 3 float4 holding rows 0 and 1
+// the addressing is 32-bit.  Links: 3 float4 per (mu, site) holding rows 0 and 1 of U
 // (row 2 rebuilt as conj(row0 x row1)).
 namespace {
 
-template <bool COMP>
+// rows 0 and 1 of a 12-real S4 link (3 float4), row 2 rebuilt as conj(row0 x row1)
 __device__ __forceinline__ void load_link_s4(const float4* __restrict__ L, int mu, int V, int site,
                                              Cx<float> U[3][3]) {
-  if (COMP) {
-    const float4* p = L + (size_t)mu * 3 * V + site;
-    const float4 a = __ldg(p), b = __ldg(p + V), c = __ldg(p + 2 * (size_t)V);
-    U[0][0] = {a.x, a.y}; U[0][1] = {a.z, a.w}; U[0][2] = {b.x, b.y};
-    U[1][0] = {b.z, b.w}; U[1][1] = {c.x, c.y}; U[1][2] = {c.z, c.w};
+  const float4* p = L + (size_t)mu * 3 * V + site;
+  const float4 a = __ldg(p), b = __ldg(p + V), c = __ldg(p + 2 * (size_t)V);
+  U[0][0] = {a.x, a.y}; U[0][1] = {a.z, a.w}; U[0][2] = {b.x, b.y};
+  U[1][0] = {b.z, b.w}; U[1][1] = {c.x, c.y}; U[1][2] = {c.z, c.w};
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
-      Cx<float> t = {U[0][j1].re * U[1][j2].re - U[0][j1].im * U[1][j2].im,
-                     U[0][j1].re * U[1][j2].im + U[0][j1].im * U[1][j2].re};
-      t.re -= U[0][j2].re * U[1][j1].re - U[0][j2].im * U[1][j1].im;
-      t.im -= U[0][j2].re * U[1][j1].im + U[0][j2].im * U[1][j1].re;
-      U[2][j] = {t.re, -t.im};
-    }
-  } else {
-    const float4* p = L + (size_t)mu * 5 * V + site;
-    float4 q[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) q[k] = __ldg(p + k * (size_t)V);
-#pragma unroll
-    for (int e = 0; e < 9; ++e) {
-      const float4 v = q[e / 2];
-      U[e / 3][e % 3] = (e & 1) ? Cx<float>{v.z, v.w} : Cx<float>{v.x, v.y};
-    }
+  for (int j = 0; j < 3; ++j) {
+    const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+    Cx<float> t = {U[0][j1].re * U[1][j2].re - U[0][j1].im * U[1][j2].im,
+                   U[0][j1].re * U[1][j2].im + U[0][j1].im * U[1][j2].re};
+    t.re -= U[0][j2].re * U[1][j1].re - U[0][j2].im * U[1][j1].im;
+    t.im -= U[0][j2].re * U[1][j1].im + U[0][j2].im * U[1][j1].re;
+    U[2][j] = {t.re, -t.im};
   }
 }
 
-template <int MU, bool COMP>
+template <int MU>
 __device__ __forceinline__ void hop_dir_s4(const float4* __restrict__ in, const float4* __restrict__ L, const Geom& g,
                                            int s, const int c[4], Cx<float> acc[12]) {
   const int V = g.V;
@@ -323,7 +311,7 @@ __device__ __forceinline__ void hop_dir_s4(const float4* __restrict__ in, const 
       else { h0[col] = cadd(p0, a0); h1[col] = cadd(p1, a1); }
     }
     Cx<float> U[3][3];
-    load_link_s4<COMP>(L, MU, V, dir == 0 ? s : sn, U);
+    load_link_s4(L, MU, V, dir == 0 ? s : sn, U);
     const float f = -0.5f * (float)sgn;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -350,19 +338,12 @@ __device__ __forceinline__ void hop_dir_s4(const float4* __restrict__ in, const 
 
 // 7 resident blocks of 128 threads per SM (<= 72 registers): the kernel waits on L2
 // latency, and the extra warps hide more of it (16^3x32, 12 RHS: 102.7 us at 80
-// registers, 97.3 us here).  CF (centre first): the diagonal term is read before the
-// hops, so that the x and y neighbours, which share its cache lines, follow it through L1.
-template <int NT>
-constexpr int s4_min_blocks() {
-  return NT == 128 ? 7 : 3;
-}
-
-template <bool COMP, int NT, bool CF>
-__global__ void __launch_bounds__(NT, s4_min_blocks<NT>()) hw32_s4_kernel(const float4* __restrict__ in,
-                                                                          float4* __restrict__ out,
-                                                                          const float4* __restrict__ L, Geom g,
-                                                                          float diag) {
-  const int s = blockIdx.x * NT + threadIdx.x;
+// registers, 97.3 us here).  The diagonal term is read before the hops, so that the x
+// and y neighbours, which share its cache lines, follow it through L1.
+constexpr int kS4NT = 128;
+__global__ void __launch_bounds__(kS4NT, 7) hw32_s4_kernel(const float4* __restrict__ in, float4* __restrict__ out,
+                                                           const float4* __restrict__ L, Geom g, float diag) {
+  const int s = blockIdx.x * kS4NT + threadIdx.x;
   if (s >= g.V) return;
   int c[4];
   site_coords(g, s, c);
@@ -373,85 +354,20 @@ __global__ void __launch_bounds__(NT, s4_min_blocks<NT>()) hw32_s4_kernel(const 
 #pragma unroll
   for (int p = 0; p < 6; ++p) {
     const int sp = p / 3, col = p % 3;
-    if (CF) {
-      const float4 v = __ldg(inr + p * V + s);
-      acc[sp * 3 + col] = cscale(diag, Cx<float>{v.x, v.y});
-      acc[(sp + 2) * 3 + col] = cscale(diag, Cx<float>{v.z, v.w});
-    } else {
-      acc[sp * 3 + col] = {0.f, 0.f};
-      acc[(sp + 2) * 3 + col] = {0.f, 0.f};
-    }
+    const float4 v = __ldg(inr + p * V + s);
+    acc[sp * 3 + col] = cscale(diag, Cx<float>{v.x, v.y});
+    acc[(sp + 2) * 3 + col] = cscale(diag, Cx<float>{v.z, v.w});
   }
-  hop_dir_s4<0, COMP>(inr, L, g, s, c, acc);
-  hop_dir_s4<1, COMP>(inr, L, g, s, c, acc);
-  hop_dir_s4<2, COMP>(inr, L, g, s, c, acc);
-  hop_dir_s4<3, COMP>(inr, L, g, s, c, acc);
+  hop_dir_s4<0>(inr, L, g, s, c, acc);
+  hop_dir_s4<1>(inr, L, g, s, c, acc);
+  hop_dir_s4<2>(inr, L, g, s, c, acc);
+  hop_dir_s4<3>(inr, L, g, s, c, acc);
 #pragma unroll
   for (int p = 0; p < 6; ++p) {
     const int sp = p / 3, col = p % 3;
-    Cx<float> up = acc[sp * 3 + col], lo = acc[(sp + 2) * 3 + col];
-    if (!CF) {
-      const float4 v = __ldg(inr + p * V + s);
-      up = cadd(cscale(diag, Cx<float>{v.x, v.y}), up);
-      lo = cadd(cscale(diag, Cx<float>{v.z, v.w}), lo);
-    }
+    const Cx<float> up = acc[sp * 3 + col], lo = acc[(sp + 2) * 3 + col];
     // upper spin sp, lower spin sp + 2 (gamma5 = -1 on it)
     outr[p * V + s] = make_float4(up.re, up.im, -lo.re, -lo.im);
-  }
-}
-
-// One hop on the S4 layout: neighbour spinor component pair p at sp[p * sps] (shared or
-// global memory), link rows 0, 1 (12-real compressed) at lk[k * lks], k = 0, 1, 2 float4
-// (row 2 rebuilt); DIR 0: forward hop (U h, h = psi_up - A psi_lo), DIR 1: backward hop
-// (U^dag h, h = psi_up + A psi_lo); f = -1/2 times the boundary sign.
-template <int MU, int DIR, bool GLOBAL>
-__device__ __forceinline__ void hop_s4(const float4* __restrict__ sp, int sps, const float4* __restrict__ lk,
-                                       int lks, float f, Cx<float> acc[12]) {
-  Cx<float> h0[3], h1[3];
-#pragma unroll
-  for (int col = 0; col < 3; ++col) {
-    const float4 a = GLOBAL ? __ldg(sp + col * sps) : sp[col * sps];        // (psi0, psi2)
-    const float4 b = GLOBAL ? __ldg(sp + (3 + col) * sps) : sp[(3 + col) * sps];  // (psi1, psi3)
-    const Cx<float> p0 = {a.x, a.y}, p2 = {a.z, a.w}, p1 = {b.x, b.y}, p3 = {b.z, b.w};
-    Cx<float> a0, a1;
-    mulA<MU>(p2, p3, a0, a1);
-    if (DIR == 0) { h0[col] = csub(p0, a0); h1[col] = csub(p1, a1); }
-    else { h0[col] = cadd(p0, a0); h1[col] = cadd(p1, a1); }
-  }
-  Cx<float> U[3][3];
-  {
-    const float4 a = lk[0], b = lk[lks], c = lk[2 * lks];
-    U[0][0] = {a.x, a.y}; U[0][1] = {a.z, a.w}; U[0][2] = {b.x, b.y};
-    U[1][0] = {b.z, b.w}; U[1][1] = {c.x, c.y}; U[1][2] = {c.z, c.w};
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
-      Cx<float> t = {U[0][j1].re * U[1][j2].re - U[0][j1].im * U[1][j2].im,
-                     U[0][j1].re * U[1][j2].im + U[0][j1].im * U[1][j2].re};
-      t.re -= U[0][j2].re * U[1][j1].re - U[0][j2].im * U[1][j1].im;
-      t.im -= U[0][j2].re * U[1][j1].im + U[0][j2].im * U[1][j1].re;
-      U[2][j] = {t.re, -t.im};
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    Cx<float> u0 = {0.f, 0.f}, u1 = {0.f, 0.f};
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      if (DIR == 0) { u0 = cfma(U[i][j], h0[j], u0); u1 = cfma(U[i][j], h1[j], u1); }
-      else { u0 = cfmaconj(U[j][i], h0[j], u0); u1 = cfmaconj(U[j][i], h1[j], u1); }
-    }
-    Cx<float> b0, b1;
-    mulAdag<MU>(u0, u1, b0, b1);
-    acc[0 * 3 + i] = cadd(acc[0 * 3 + i], cscale(f, u0));
-    acc[1 * 3 + i] = cadd(acc[1 * 3 + i], cscale(f, u1));
-    if (DIR == 0) {
-      acc[2 * 3 + i] = csub(acc[2 * 3 + i], cscale(f, b0));
-      acc[3 * 3 + i] = csub(acc[3 * 3 + i], cscale(f, b1));
-    } else {
-      acc[2 * 3 + i] = cadd(acc[2 * 3 + i], cscale(f, b0));
-      acc[3 * 3 + i] = cadd(acc[3 * 3 + i], cscale(f, b1));
-    }
   }
 }
 
@@ -481,18 +397,15 @@ __global__ void unpack_s4_kernel(const float4* __restrict__ s4, float2* __restri
   }
 }
 
-// U32 planes (mu*9 + e, site) -> S4 links: 5 float4 (pairs of elements) or 3 (rows 0, 1)
-__global__ void links_s4_kernel(const float2* __restrict__ u32, float4* __restrict__ l5, float4* __restrict__ l3,
-                                int V) {
+// U32 planes (mu*9 + e, site) -> 12-real S4 links: 3 float4 holding rows 0 and 1 in
+// element pairs (U00, U01), (U02, U10), (U11, U12)
+__global__ void links_s4_kernel(const float2* __restrict__ u32, float4* __restrict__ l3, int V) {
   const size_t n = (size_t)4 * V;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
     const size_t site = t % V, mu = t / V;
-    float2 e[10];
+    float2 e[6];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) e[k] = u32[(mu * 9 + k) * V + site];
-    e[9] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) l5[(mu * 5 + k) * V + site] = make_float4(e[2 * k].x, e[2 * k].y, e[2 * k + 1].x, e[2 * k + 1].y);
+    for (int k = 0; k < 6; ++k) e[k] = u32[(mu * 9 + k) * V + site];
 #pragma unroll
     for (int k = 0; k < 3; ++k) l3[(mu * 3 + k) * V + site] = make_float4(e[2 * k].x, e[2 * k].y, e[2 * k + 1].x, e[2 * k + 1].y);
   }
@@ -518,36 +431,28 @@ int launch_unpack_s4(ov_ctx* ctx, const float4* s4, float2* aos, int nrhs, cudaS
   return OV_OK;
 }
 
-// The S4 link forms (built together on first use after set_gauge): comp = true gives
-// the 3-float4 (12-real) links, false the 5-float4 (padded pairs) links.
-const float4* s4_links(ov_ctx* ctx, bool comp, cudaStream_t s, int* st) {
-  float4* l5 = (float4*)ws_get(ctx, "gauge.s4l5", sizeof(float4) * 4 * 5 * (size_t)ctx->g.V, st);
+// The 12-real S4 links (3 float4 per link, built on first use after set_gauge); the
+// right-hand-side-paired kernels read the same form.
+const float4* s4_links(ov_ctx* ctx, cudaStream_t s, int* st) {
   float4* l3 = (float4*)ws_get(ctx, "gauge.s4l3", sizeof(float4) * 4 * 3 * (size_t)ctx->g.V, st);
   if (*st != OV_OK) return nullptr;
   if (!ctx->have_s4) {
-    links_s4_kernel<<<cap_grid32((size_t)4 * ctx->g.V), 256, 0, s>>>(ctx->U32, l5, l3, ctx->g.V);
+    links_s4_kernel<<<cap_grid32((size_t)4 * ctx->g.V), 256, 0, s>>>(ctx->U32, l3, ctx->g.V);
     ctx->have_s4 = true;
   }
-  return comp ? l3 : l5;
+  return l3;
 }
 
-// out = H_W in on the S4 layout with the 3-float4 (12-real) links; comp 3 and 4: reading
-// the centre first, with 128 or 256 threads per block.
-int launch_hw32_s4(ov_ctx* ctx, const float4* in, float4* out, int nrhs, int comp, cudaStream_t s) {
+// out = H_W in on the S4 layout with the 12-real links, one RHS per thread.
+int launch_hw32_s4(ov_ctx* ctx, const float4* in, float4* out, int nrhs, cudaStream_t s) {
   int st = OV_OK;
-  const float4* l3 = s4_links(ctx, true, s, &st);
+  const float4* l3 = s4_links(ctx, s, &st);
   if (st != OV_OK) return st;
   const float diag = (float)(4.0 - ctx->m0);
-  const int NT = comp == 4 ? 256 : 128;
-  dim3 grid((ctx->g.V + NT - 1) / NT, nrhs);
+  dim3 grid((ctx->g.V + kS4NT - 1) / kS4NT, nrhs);
   cudaEvent_t ev;
   kt_begin(ctx, KC_DSLASH, s, &ev);
-  if (comp == 4)
-    hw32_s4_kernel<true, 256, true><<<grid, NT, 0, s>>>(in, out, l3, ctx->g, diag);
-  else if (comp == 3)
-    hw32_s4_kernel<true, 128, true><<<grid, NT, 0, s>>>(in, out, l3, ctx->g, diag);
-  else
-    hw32_s4_kernel<true, 128, false><<<grid, NT, 0, s>>>(in, out, l3, ctx->g, diag);
+  hw32_s4_kernel<<<grid, kS4NT, 0, s>>>(in, out, l3, ctx->g, diag);
   kt_end(ctx, KC_DSLASH, s, ev);
   OV_CHECK_LAUNCH(ctx, "hw32_s4_kernel");
   return OV_OK;

@@ -172,12 +172,12 @@ int ensure_links_df(ov_ctx* ctx, cudaStream_t s);
 // spin-paired float4 FP32 layout (dslash32.cu)
 int launch_pack_s4(ov_ctx* ctx, const float2* aos, float4* s4, int nrhs, cudaStream_t s);
 int launch_unpack_s4(ov_ctx* ctx, const float4* s4, float2* aos, int nrhs, cudaStream_t s);
-int launch_hw32_s4(ov_ctx* ctx, const float4* in, float4* out, int nrhs, int comp, cudaStream_t s);
+int launch_hw32_s4(ov_ctx* ctx, const float4* in, float4* out, int nrhs, cudaStream_t s);
 // paired FP32 layout (pair32.cu)
 int launch_pack_pair32(ov_ctx* ctx, const float2* aos, float4* pr, int nrhs, cudaStream_t s);
 int launch_unpack_pair32(ov_ctx* ctx, const float4* pr, float2* aos, int nrhs, cudaStream_t s);
 int launch_hw_pair12(ov_ctx* ctx, const float4* in, float4* out, int npair, int form, cudaStream_t s);
-const float4* s4_links(ov_ctx* ctx, bool comp, cudaStream_t s, int* st);
+const float4* s4_links(ov_ctx* ctx, cudaStream_t s, int* st);
 // out(AoS) = (1+m)/2 b(AoS) + (1-m)/2 gamma5 s(SoA)
 int launch_overlap_epilogue(ov_ctx* ctx, const double2* b_aos, const double2* s_soa, double2* out_aos,
                             double m_q, int nrhs, cudaStream_t s);

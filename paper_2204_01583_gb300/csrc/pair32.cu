@@ -95,29 +95,22 @@ int launch_unpack_pair32(ov_ctx* ctx, const float4* pr, float2* aos, int nrhs, c
   return OV_OK;
 }
 
-// form 1: the spin-paired layout's 3 float4 per link (48 B); 2 and 3: form 1 reading the
-// centre first, 128 or 256 threads per block; 4: form 2 with all 9 link elements read
-// (the spin-paired layout's padded 5 float4, 80 B), no rebuild; 6: form 2 with row 2
-// rebuilt in scalar arithmetic.
+// form 2: compact 12-real links (the spin-paired layout's 3 float4 per link, 48 B), the
+// centre read first, 128 threads per block; form 6: the same with row 2 rebuilt once in
+// scalar arithmetic.
 int launch_hw_pair12(ov_ctx* ctx, const float4* in, float4* out, int npair, int form, cudaStream_t s) {
   int st = OV_OK;
-  const float4* L = s4_links(ctx, form != 4, s, &st);
+  const float4* L = s4_links(ctx, s, &st);
   if (st != OV_OK) return st;
-  const int NT = form == 3 ? 256 : 128;
+  constexpr int NT = 128;
   dim3 grid(npair, (ctx->g.V + NT - 1) / NT);
   const float diag = (float)(4.0 - ctx->m0);
   cudaEvent_t ev;
   kt_begin(ctx, KC_DSLASH, s, &ev);
-  if (form == 1)
-    hw_pair12_kernel<1, 128, false><<<grid, NT, 0, s>>>(in, out, L, ctx->g, diag);
-  else if (form == 2)
-    hw_pair12_kernel<1, 128, true><<<grid, NT, 0, s>>>(in, out, L, ctx->g, diag);
-  else if (form == 3)
-    hw_pair12_kernel<1, 256, true><<<grid, NT, 0, s>>>(in, out, L, ctx->g, diag);
-  else if (form == 4)
-    hw_pair12_kernel<2, 128, true><<<grid, NT, 0, s>>>(in, out, L, ctx->g, diag);
+  if (form == 6)
+    hw_pair12_kernel<3, NT, true><<<grid, NT, 0, s>>>(in, out, L, ctx->g, diag);
   else
-    hw_pair12_kernel<3, 128, true><<<grid, NT, 0, s>>>(in, out, L, ctx->g, diag);
+    hw_pair12_kernel<1, NT, true><<<grid, NT, 0, s>>>(in, out, L, ctx->g, diag);
   kt_end(ctx, KC_DSLASH, s, ev);
   OV_CHECK_LAUNCH(ctx, "hw_pair12_kernel");
   return OV_OK;

@@ -96,19 +96,6 @@ __device__ __forceinline__ void link12_rows(const float4* __restrict__ L, int mu
   U[1][0] = bc2(b.z, b.w); U[1][1] = bc2(c.x, c.y); U[1][2] = bc2(c.z, c.w);
 }
 
-// all 9 elements from the spin-paired layout's padded form: 5 float4 per link holding
-// the elements row-major in pairs, (U00, U01), (U02, U10), ..., (U22, 0)
-__device__ __forceinline__ void link9_rows(const float4* __restrict__ L, int mu, int V, int site, B2 U[3][3]) {
-  const float4* p = L + (size_t)mu * 5 * V + site;
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const float4 v = __ldg(p + k * (size_t)V);
-    const int e = 2 * k;
-    U[e / 3][e % 3] = bc2(v.x, v.y);
-    if (e + 1 < 9) U[(e + 1) / 3][(e + 1) % 3] = bc2(v.z, v.w);
-  }
-}
-
 // compact 12-real link with row 2 rebuilt once in scalar arithmetic (both lanes of a
 // pair would compute the same value), then all 9 elements as lane-equal pairs
 __device__ __forceinline__ void link12_scalar(const float4* __restrict__ L, int mu, int V, int site, B2 U[3][3]) {
@@ -147,9 +134,8 @@ __device__ __forceinline__ B2 link12_row2(const B2 U[3][3], int j) {
 // Both hops of direction MU for one site and the two right-hand sides of a pair, with
 // 12-real links.  Upper spins accumulate +f u, lower spins the NEGATED contribution
 // (the caller applies gamma5 = -1 on them by adding -diag psi_lo at the end).
-// LK 1: compact 12-real links, 2: all 9 elements (padded
-// 5-float4 form, no rebuild), 3: compact 12-real links with row 2 rebuilt in scalar
-// arithmetic.
+// LK 1: compact 12-real links, row 2 rebuilt element by element in paired arithmetic;
+// 3: compact 12-real links with row 2 rebuilt once in scalar arithmetic.
 template <int MU, int LK>
 __device__ __forceinline__ void hop_pair12(const float4* __restrict__ in, const float4* __restrict__ L,
                                            const Geom& g, int s, const int c[4], P2 acc[12]) {
@@ -172,9 +158,7 @@ __device__ __forceinline__ void hop_pair12(const float4* __restrict__ in, const 
         proj_pair<MU, 1>(p0, p1, p2, p3, h0[col], h1[col]);
     }
     B2 U[3][3];
-    if (LK == 2)
-      link9_rows(L, MU, V, sl, U);
-    else if (LK == 3)
+    if (LK == 3)
       link12_scalar(L, MU, V, sl, U);
     else
       link12_rows(L, MU, V, sl, U);
@@ -191,7 +175,7 @@ __device__ __forceinline__ void hop_pair12(const float4* __restrict__ in, const 
       for (int j = 0; j < 3; ++j) {
         // row 2 is rebuilt element by element where it is used
         const int r = dir == 0 ? i : j, q = dir == 0 ? j : i;
-        const B2 l = (r < 2 || LK >= 2) ? U[r][q] : link12_row2(U, q);
+        const B2 l = (r < 2 || LK == 3) ? U[r][q] : link12_row2(U, q);
         const float2 nli = f2(-l.im.x, -l.im.y);
         a0 = fma2(l.re, h0[j].re, a0);
         a1 = fma2(l.re, h1[j].re, a1);

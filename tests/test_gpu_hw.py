@@ -82,13 +82,13 @@ def test_hw_rejects_bad_arguments(gpu_lib):
     assert e.value.code == gpu_lib.OV_ERR_NO_GAUGE
 
 
-@pytest.mark.parametrize("variant", list(range(17)))
+@pytest.mark.parametrize("variant", list(range(6)))
 def test_hw_fp32_variants(gpu_lib, variant):
     """Every FP32 stencil variant (RHS tile, link compression, block size) against the
     oracle, with a right-hand-side count that leaves a ragged last tile."""
     import torch
 
-    assert len(gpu_lib.hw32_variants()) == 17
+    assert len(gpu_lib.hw32_variants()) == 6
     dims = (6, 4, 5, 4)
     ctx, U = make_ctx(gpu_lib, dims, 0.6, 71)
     ctx.set_hw32_variant(variant)
