@@ -1,10 +1,8 @@
-// Kernels on the right-hand-side-paired FP32 layout (see pair32.cuh): broadcast
-// links, packing from and to the canonical layout, and H_W.
+// Kernels on the right-hand-side-paired FP32 layout (see pair32.cuh): packing from and
+// to the canonical layout, and H_W.
 #include "pair32.cuh"
 
 namespace {
-
-constexpr int kNTP = 128;
 
 // canonical complex64 [rhs][site][12] -> pairs; a missing partner of an odd count is 0
 __global__ void pack_pair_f32_kernel(const float2* __restrict__ aos, float4* __restrict__ pr, int V, int nrhs) {
@@ -32,10 +30,10 @@ __global__ void unpack_pair_f32_kernel(const float4* __restrict__ pr, float2* __
 
 // H_W on the paired layout with 12-real links.  grid: x = pair, y = block of sites.
 // At most 128 registers (4 blocks of 128 threads per SM): 12 accumulator pairs, the
-// half spinor and the rebuilt link are live together.
-// CF (centre first): the diagonal term is read before the hops, so that the x and y
-// neighbours, which share its cache lines, follow it through L1.
-template <int LK, int NT, bool CF>
+// half spinor and the rebuilt link are live together.  The diagonal term is read before
+// the hops, so that the x and y neighbours, which share its cache lines, follow it
+// through L1.
+template <int LK, int NT>
 __global__ void __launch_bounds__(NT, 512 / NT) hw_pair12_kernel(const float4* __restrict__ in,
                                                                  float4* __restrict__ out,
                                                                  const float4* __restrict__ L, Geom g, float diag) {
@@ -49,28 +47,16 @@ __global__ void __launch_bounds__(NT, 512 / NT) hw_pair12_kernel(const float4* _
   P2 o[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
-    if (CF) {
-      const P2 v = ldp(inq + k * (size_t)g.V + s);
-      const float2 d = k < 6 ? d2 : nd2;  // lower spins: gamma5 = -1, accumulated negated
-      o[k] = {mul2(d, v.re), mul2(d, v.im)};
-    } else {
-      o[k] = {f2(0.f, 0.f), f2(0.f, 0.f)};
-    }
+    const P2 v = ldp(inq + k * (size_t)g.V + s);
+    const float2 d = k < 6 ? d2 : nd2;  // lower spins: gamma5 = -1, accumulated negated
+    o[k] = {mul2(d, v.re), mul2(d, v.im)};
   }
   hop_pair12<0, LK>(inq, L, g, s, c, o);
   hop_pair12<1, LK>(inq, L, g, s, c, o);
   hop_pair12<2, LK>(inq, L, g, s, c, o);
   hop_pair12<3, LK>(inq, L, g, s, c, o);
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    P2 r = o[k];
-    if (!CF) {
-      const P2 v = ldp(inq + k * (size_t)g.V + s);
-      const float2 d = k < 6 ? d2 : nd2;
-      r = {fma2(d, v.re, r.re), fma2(d, v.im, r.im)};
-    }
-    stp(out + off + k * (size_t)g.V + s, r);
-  }
+  for (int k = 0; k < 12; ++k) stp(out + off + k * (size_t)g.V + s, o[k]);
 }
 
 int cap_grid(size_t n) {
@@ -108,9 +94,9 @@ int launch_hw_pair12(ov_ctx* ctx, const float4* in, float4* out, int npair, int 
   cudaEvent_t ev;
   kt_begin(ctx, KC_DSLASH, s, &ev);
   if (form == 6)
-    hw_pair12_kernel<3, NT, true><<<grid, NT, 0, s>>>(in, out, L, ctx->g, diag);
+    hw_pair12_kernel<3, NT><<<grid, NT, 0, s>>>(in, out, L, ctx->g, diag);
   else
-    hw_pair12_kernel<1, NT, true><<<grid, NT, 0, s>>>(in, out, L, ctx->g, diag);
+    hw_pair12_kernel<1, NT><<<grid, NT, 0, s>>>(in, out, L, ctx->g, diag);
   kt_end(ctx, KC_DSLASH, s, ev);
   OV_CHECK_LAUNCH(ctx, "hw_pair12_kernel");
   return OV_OK;
