@@ -1212,12 +1212,16 @@ SolveArgs<R> args_for_sources(const SolveWs<R>& w, int r0) {
 // Source groups of a replayed graph.  Sources are independent, so the per-iteration
 // kernels of G groups can run as parallel branches of one graph: on small lattices, where
 // a launch leaves SMs idle through its tail, its serial last-block step and the next
-// launch's ramp, each branch fills the other's gaps.  Auto: one group per source, at most
-// four, when the stencil grid of all sources fits two waves (152 SMs x 4 blocks); else one.
-// (8^4, 4 sources, FP64 two-pass: 23.8 / 22.6 / 22.0 ms per apply with 1 / 2 / 4 groups.)
+// launch's ramp, each branch fills the other's gaps; on large ones one branch's update
+// kernel (bound by HBM) runs beside the other's stencil kernel (bound by the FP64 pipe or
+// FP32 issue).  Auto: one group per source, at most four, when the stencil grid of all
+// sources fits two waves (152 SMs x 4 blocks); else two.
+// (8^4, 4 sources, FP64 two-pass: 23.8 / 22.6 / 22.0 ms per apply with 1 / 2 / 4 groups;
+// 16^3 x 32, 12 sources in batches of 6: FP64 two-pass 1385 / 1373 ms, double-float 407
+// / 390 ms with 1 / 2 groups; 16^4: 533.6 / 529.8 ms.)
 int source_groups(const ov_ctx* ctx, int nsrc, int nblk1) {
   int g = ctx->groups;
-  if (g <= 0) g = ((size_t)nblk1 * nsrc <= (size_t)2 * 152 * 4) ? 4 : 1;
+  if (g <= 0) g = ((size_t)nblk1 * nsrc <= (size_t)2 * 152 * 4) ? 4 : 2;
   return std::max(1, std::min(g, nsrc));
 }
 
