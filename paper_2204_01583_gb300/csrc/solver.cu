@@ -1215,13 +1215,14 @@ SolveArgs<R> args_for_sources(const SolveWs<R>& w, int r0) {
 // launch's ramp, each branch fills the other's gaps; on large ones one branch's update
 // kernel (bound by HBM) runs beside the other's stencil kernel (bound by the FP64 pipe or
 // FP32 issue).  Auto: one group per source, at most four, when the stencil grid of all
-// sources fits two waves (152 SMs x 4 blocks); else two.
+// sources fits two waves (152 SMs x 4 blocks); else two, or six for double-float.
 // (8^4, 4 sources, FP64 two-pass: 23.8 / 22.6 / 22.0 ms per apply with 1 / 2 / 4 groups;
-// 16^3 x 32, 12 sources in batches of 6: FP64 two-pass 1385 / 1373 ms, double-float 407
-// / 390 ms with 1 / 2 groups; 16^4: 533.6 / 529.8 ms.)
+// 16^3 x 32, 12 sources in batches of 6, 1 / 2 / 3 / 6 groups: FP64 two-pass 1385 / 1373
+// / 1374 / 1375 ms, double-float 407 / 390 / 390 / 386 ms; 16^4: 533.6 / 529.8 ms.)
+template <typename R>
 int source_groups(const ov_ctx* ctx, int nsrc, int nblk1) {
   int g = ctx->groups;
-  if (g <= 0) g = ((size_t)nblk1 * nsrc <= (size_t)2 * 152 * 4) ? 4 : 2;
+  if (g <= 0) g = ((size_t)nblk1 * nsrc <= (size_t)2 * 152 * 4) ? 4 : (std::is_same<R, DF>::value ? 6 : 2);
   return std::max(1, std::min(g, nsrc));
 }
 
@@ -1370,7 +1371,7 @@ int run_iterations(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, int nshift, int f
   const bool graph = o.use_graph && !ctx->timing;
   cudaGraphExec_t exec = nullptr;
   if (graph) {
-    const int G = source_groups(ctx, nsrc, w.nblk1);
+    const int G = source_groups<R>(ctx, nsrc, w.nblk1);
     GraphKey key{{(const void*)w.a.ring, (const void*)w.a.p, (const void*)w.a.x, (const void*)w.a.sacc},
                  nsrc, nshift, flavour * 128 + G, chunk, w.nslots, w.max_iter};
     auto it = ctx->graphs.find(key);
@@ -1393,7 +1394,7 @@ int run_iterations(ov_ctx* ctx, const SolveWs<R>& w, int nsrc, int nshift, int f
       ctx->graphs[key] = exec;
     }
   }
-  const int G = graph ? source_groups(ctx, nsrc, w.nblk1) : 1;
+  const int G = graph ? source_groups<R>(ctx, nsrc, w.nblk1) : 1;
   int done_iters = 0;
   while (done_iters < max_iter) {
     const int n = std::min(chunk, max_iter - done_iters);
@@ -1895,7 +1896,7 @@ static int solve_sign_regen(ov_ctx* ctx, const double2* b_soa, double2* out_soa,
   const bool graph = o.use_graph && !ctx->timing;
   cudaGraphExec_t exec = nullptr;
   if (graph && kmax >= chunk) {
-    const int G = source_groups(ctx, nsrc, w.nblk1);
+    const int G = source_groups<R>(ctx, nsrc, w.nblk1);
     GraphKey key{{(const void*)w.a.ring, (const void*)gco, (const void*)w.a.sacc, (const void*)w.a.hist_a},
                  nsrc, ns, 3 * 128 + G, chunk, w.nslots, w.max_iter};
     auto it = ctx->graphs.find(key);
@@ -1912,7 +1913,7 @@ static int solve_sign_regen(ov_ctx* ctx, const double2* b_soa, double2* out_soa,
       ctx->graphs[key] = exec;
     }
   }
-  const int Gr = exec ? source_groups(ctx, nsrc, w.nblk1) : 1;
+  const int Gr = exec ? source_groups<R>(ctx, nsrc, w.nblk1) : 1;
   int done = 0;
   while (done < kmax) {
     const int n = std::min(chunk, kmax - done);
