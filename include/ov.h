@@ -298,10 +298,12 @@ int ov_set_persistent(ov_ctx* ctx, int enable);
 /* Scheduling of independent sources (no counterpart in the paper).
  * Sources of one call are independent; the per-iteration kernels replayed from a CUDA
  * graph can run as `groups` parallel branches, each over a contiguous block of sources,
- * which fills the launch tails and serial reduction steps of small lattices.  groups = 0
- * (default): one branch per source, at most four, when the stencil grid of all sources
- * fits two waves of the GPU, else one; groups >= 1: that many (capped at the source
- * count).  Results do not depend on it (every source's arithmetic is the same).
+ * which fills the launch tails and serial reduction steps of small lattices and, on large
+ * ones, runs one branch's vector update beside another's stencil.  groups = 0 (default):
+ * one branch per source, at most four, when the stencil grid of all sources fits two
+ * waves of the GPU, else two (six for the double-float mode); groups >= 1: that many
+ * (capped at the source count of a batch).  Results do not depend on it (every source's
+ * arithmetic is the same).
  * Errors: OV_ERR_INVALID_ARG for groups outside [0, 64]. */
 int ov_set_concurrency(ov_ctx* ctx, int groups);
 
